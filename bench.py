@@ -1,0 +1,367 @@
+"""Benchmark: batched Roaring set operations on one GB300 (or N replicas).
+
+Workload (the batched configuration): a pool of 4096 seeded bitmaps over
+[0, 2^32), cardinalities log-uniform 10..1e7, classes 40% uniform-sparse /
+30% dense-clustered / 30% runs; 65,536 query pairs (a != b) with ops AND 40% /
+OR 30% / ANDNOT 15% / XOR 15%, materialised as canonical Roaring bitmaps,
+plus a count-only Jaccard batch over the same pairs.
+
+One step = one run of both batches (two persistent launches replayed from
+CUDA graphs, plus compaction).  value = sum over pairs of (|A| + |B|) per
+step / device time of the step, in Gints/s (the paper's per-input-value
+normalisation inverted); pairs are counted once per step although the Jaccard
+batch reads them again.  The pool (3+ GB) and the outputs (tens of GB) are far
+larger than L2, so no flush is needed between steps.
+
+--impl reference times the CPU oracle (test infrastructure, plain C) on the
+host cores over a bounded sample of the same pairs.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PAIRS = 65536
+DOMINANT = "k_pairs (materialising batch)"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(seed_offset=0):
+    import workloads as W
+    t0 = time.time()
+    pool = W.make_pool(W.SPECS["batched"])
+    ops, a, b = W.pairs(4 + seed_offset, N_PAIRS, pool.n)
+    log(f"generated pool of {pool.n} bitmaps ({int(pool.sizes().sum()):,} values) in {time.time() - t0:.1f}s")
+    return pool, ops, a, b
+
+
+def cpu_oracle_leg(pool, ops, a, b, budget_s=15.0, threads=None):
+    """Time the oracle (as it stands) on the host cores over a bounded sample
+    of the pairs: the materialised op plus the Jaccard counts of each pair."""
+    import oracle
+    oracle.build()
+    threads = threads or os.cpu_count() or 1
+    sizes = pool.sizes()
+    order = np.arange(len(ops))
+    # build the oracle bitmaps of a prefix of the pairs (not timed)
+    sample = []
+    need = set()
+    est_vals = 0
+    for i in order:
+        sample.append(int(i))
+        need.update([int(a[i]), int(b[i])])
+        est_vals += int(sizes[a[i]]) + int(sizes[b[i]])
+        if est_vals > 3e8 or len(sample) >= 2048:
+            break
+    with cf.ThreadPoolExecutor(threads) as ex:
+        built = dict(zip(sorted(need), ex.map(lambda j: oracle.Bitmap.from_sorted(pool.values(j)), sorted(need))))
+
+    def one(i):
+        A, B = built[int(a[i])], built[int(b[i])]
+        r = A.op(int(ops[i]), B)
+        c = r.card
+        r.close()
+        A.jaccard(B)
+        return int(sizes[a[i]]) + int(sizes[b[i]]), c
+
+    done_vals, done_pairs = 0, 0
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        futs = []
+        for i in sample:
+            futs.append(ex.submit(one, i))
+        for f in futs:
+            v, _ = f.result()
+            done_vals += v
+            done_pairs += 1
+            if time.perf_counter() - t0 > budget_s:
+                for g in futs:
+                    g.cancel()
+                break
+    dt = time.perf_counter() - t0
+    for x in built.values():
+        x.close()
+    return {"value": done_vals / dt / 1e9, "unit": "Gints/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {done_pairs} of the {len(ops)} pairs (materialised op + Jaccard each), "
+                      f"{done_vals:,} input values, {dt:.1f}s on {threads} host threads"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    pool, ops, a, b = make_workload()
+    steps = []
+    res = None
+    for s in range(args.warmup + args.steps):
+        res = cpu_oracle_leg(pool, ops, a, b, budget_s=args.ref_budget)
+        if s >= args.warmup:
+            steps.append(res["value"])
+    value = statistics.median(steps)
+    line = {"impl": "reference", "metric": "batched Roaring AND/OR Gints/s", "value": value, "unit": "Gints/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16/u64 integer", "data": "synthetic (seeded)",
+            "config": {"workload": "batched: 4096-bitmap pool over [0,2^32), c log-uniform 10..1e7, "
+                                   "40/30/30 sparse/dense/runs; 65,536 pairs AND/OR/ANDNOT/XOR 40/30/15/15 "
+                                   "materialised + Jaccard", "global_batch": N_PAIRS},
+            "cpu_baseline": dict(res, value=value),
+            "e2e": {"value": value, "unit": "Gints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1709_07821_gb300 as rb
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rb.build()
+    rb.lib()
+
+    pool, ops, a, b = make_workload(seed_offset=rank)
+    sizes = pool.sizes().astype(np.float64)
+    units = float((sizes[a] + sizes[b]).sum())      # input values per step (pairs counted once)
+
+    t0 = time.time()
+    G = []
+    for i in range(pool.n):
+        G.append(rb.Bitmap.from_sorted(pool.values(i)))
+    torch.cuda.synchronize()
+    pool_bytes = sum(g.payload_bytes() + 10 * g.n_containers for g in G)
+    log(f"rank {rank}: built {len(G)} device bitmaps ({pool_bytes / 1e9:.2f} GB) in {time.time() - t0:.1f}s")
+
+    plan_m = rb.Plan(G, ops, a, b)
+    jflags = np.full(N_PAIRS, rb.Q_COUNT_ONLY, np.uint32)
+    plan_j = rb.Plan(G, np.zeros(N_PAIRS, np.uint32), a, b, jflags)
+
+    if args.autotune:
+        best, ms = plan_m.autotune(reps=1)
+        log(f"autotune: {best} ({ms:.2f} ms)")
+
+    stream = torch.cuda.current_stream()
+
+    def step():
+        outs, counts = plan_m.run()
+        _, inter = plan_j.run()
+        return outs, counts, inter
+
+    for _ in range(args.warmup):
+        outs, _, _ = step()
+        for o in outs:
+            if o is not None:
+                o.free()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local) if rank == 0 else None
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, alg, outb, step_ms = [], [], [], []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        outs, counts, inter = step()
+        s1.record(stream)
+        st = plan_m.stats()
+        kms.append(st["kernel_ms"])
+        alg.append(st["alg_bytes"])
+        outb.append(st["out_bytes"])
+        for o in outs:
+            if o is not None:
+                o.free()
+        s1.synchronize()
+        step_ms.append(s0.elapsed_time(s1))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop() if clocks else None
+    t = torch.tensor([total_ms], device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+    total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = units * ws / (ms_per_step / 1e3) / 1e9
+
+    # end to end through the public API: queries from host memory, counts back
+    # to host, one rb_batch_op + rb_batch_jaccard per step (no plan reuse)
+    e2e_steps = max(1, min(args.steps, 3))
+    t1 = time.perf_counter()
+    for _ in range(e2e_steps):
+        bms, cnt = rb.batch_op(G, ops, a, b)
+        jj, ii, uu = rb.batch_jaccard(G, a, b)
+        for o in bms:
+            if o is not None:
+                o.free()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t1) / e2e_steps
+    h2d = 2 * (32 * len(G) + 32 * N_PAIRS + 8 * (N_PAIRS + 1) + 128) + 2 * 16 * N_PAIRS
+    d2h = 2 * (40 * N_PAIRS + 128) + 8 * N_PAIRS * 4
+    e2e = {"value": units / e2e_s / 1e9, "unit": "Gints/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "what": "rb_batch_op + rb_batch_jaccard from host query arrays, counts/Jaccard to host; "
+                   "index resident on the device"}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peaks()
+    kernel_ms = statistics.mean(kms)
+    alg_bytes = statistics.mean(alg)
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": args.traffic, "kernel": DOMINANT, "kernel_ms": kernel_ms,
+                "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
+
+    # per-pair baseline on the same GPU: rb_apply one pair at a time
+    per = per_pair_leg(rb, G, ops, a, b, sizes, n=args.per_pair_sample)
+    cpu = cpu_oracle_leg(pool, ops, a, b, budget_s=args.cpu_budget) if not args.no_cpu else None
+
+    line = {"metric": "batched Roaring AND/OR Gints/s", "value": value, "unit": "Gints/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u16/u64 integer", "data": "synthetic (seeded)",
+            "config": {"workload": "batched: 4096-bitmap pool over [0,2^32), c log-uniform 10..1e7, 40/30/30 "
+                                   "sparse/dense/runs; 65,536 pairs AND/OR/ANDNOT/XOR 40/30/15/15 materialised "
+                                   "+ Jaccard count batch", "global_batch": N_PAIRS * ws,
+                       "pool_bytes": pool_bytes, "units_per_step": units,
+                       "l2": "inputs larger than L2 (pool and outputs are GBs), no flush",
+                       "parallelism": f"replicas x{ws}", "schedule": rb.get_schedule()},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
+            "per_pair": per}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def per_pair_leg(rb, G, ops, a, b, sizes, n=512):
+    """The same pairs through rb_apply + rb_jaccard one pair at a time."""
+    import torch
+    if n <= 0:
+        return None
+    idx = np.arange(n)
+    lat = []
+    vals = 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in idx:
+        s = time.perf_counter()
+        r = G[a[i]].op(int(ops[i]), G[b[i]])
+        G[a[i]].jaccard(G[b[i]])
+        lat.append((time.perf_counter() - s) * 1e3)
+        r.free()
+        vals += sizes[a[i]] + sizes[b[i]]
+    dt = time.perf_counter() - t0
+    return {"gints_s": vals / dt / 1e9, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "sample_pairs": int(n),
+            "what": "rb_apply + rb_jaccard per pair (one launch sequence and host sync per call)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--per-pair-sample", type=int, default=512)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="dram bytes per launch of the dominant kernel from an ncu capture")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

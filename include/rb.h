@@ -1,0 +1,249 @@
+/*
+ * rb.h - C ABI of the GB300 (sm_103a) Roaring bitmap library.
+ *
+ * A Roaring bitmap stores a set of 32-bit integers as a sorted list of 16-bit
+ * keys (the high halves present in the set), each paired with one container
+ * holding the low halves of that chunk: a bitset of 2^16 bits, an array of at
+ * most 4096 sorted values, or a list of runs <s,l> meaning [s, s+l]
+ * (arXiv 1709.07821, Sec. 1, Fig. 1).  Every bitmap this library hands out is
+ * in canonical form: no empty container, and each container of cardinality c
+ * with r maximal runs is a run container iff (c <= 4096 and 2r < c) or
+ * (c > 4096 and r <= 2047), else an array iff c <= 4096, else a bitset
+ * (Sec. 1's type constraints, read as "smallest of array 2c B, bitset 8 KB,
+ * runs 4r B").
+ *
+ * Conventions for every entry point:
+ *  - Bitmaps live in device memory of the current CUDA device; rb_t is an
+ *    opaque host handle.  Inputs are never modified (Sec. 5: operations build
+ *    a new bitmap and leave their inputs unchanged).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that return host-visible results (counts, new handles) synchronise that
+ *    stream before returning.
+ *  - Every rb_t** output is a new handle owned by the caller and released
+ *    with rb_free().  On error *out is set to NULL and nothing leaks.
+ *  - Errors: each call returns an rb_status; rb_last_error() gives a message
+ *    for the calling thread's last failure.
+ *  - Device memory comes from the allocator installed with
+ *    rb_set_allocator() (default: cudaMallocAsync / cudaFreeAsync).
+ */
+#ifndef RB_H
+#define RB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rb rb_t;
+
+typedef enum {
+    RB_OK = 0,
+    RB_EINVAL = 1,    /* bad argument: NULL handle, unsorted input, bad op ... */
+    RB_ENOMEM = 2,    /* the allocator returned NULL */
+    RB_ECUDA = 3,     /* a CUDA runtime call failed (message has the reason) */
+    RB_ETIMEOUT = 4,  /* a bounded wait ran out */
+    RB_EBUSY = 5,     /* admission refused: not enough budget right now */
+    RB_ERANGE = 6     /* a size exceeds a documented limit */
+} rb_status;
+
+/* Sec. 1: intersection = AND, union = OR, difference = ANDNOT,
+ * symmetric difference = XOR. */
+typedef enum { RB_AND = 0, RB_OR = 1, RB_ANDNOT = 2, RB_XOR = 3 } rb_op;
+
+/* container type codes used by rb_export_layout */
+enum { RB_TYPE_ARRAY = 0, RB_TYPE_BITSET = 1, RB_TYPE_RUN = 2 };
+
+/* ---------------------------------------------------------------- memory */
+
+/* Device allocator hooks.  alloc returns a device pointer (16-byte aligned at
+ * least) or NULL; release gets back the pointer and size it was given.  The
+ * stream is the one the memory is first used on.  Passing NULL for both
+ * restores the default (cudaMallocAsync / cudaFreeAsync). */
+typedef void *(*rb_alloc_fn)(uint64_t bytes, void *stream, void *ctx);
+typedef void (*rb_free_fn)(void *ptr, uint64_t bytes, void *stream, void *ctx);
+rb_status rb_set_allocator(rb_alloc_fn alloc, rb_free_fn release, void *ctx);
+
+/* --------------------------------------------------------- construction */
+
+/* Build a bitmap from n strictly increasing uint32 values (Sec. 1: chunk by
+ * the high 16 bits, keep the low 16 bits in the chunk's container, type
+ * chosen by the canonical rule).  `vals` is a device pointer if
+ * vals_on_device != 0, else host memory (copied in on `stream`).  Unsorted or
+ * duplicate input returns RB_EINVAL.  n == 0 gives the empty bitmap. */
+rb_status rb_from_sorted_u32(const uint32_t *vals, uint64_t n, int vals_on_device, void *stream,
+                             rb_t **out);
+
+/* Write the set's values in ascending order to dst (device memory if
+ * dst_on_device != 0, else host memory), at most cap of them; *n_out gets the
+ * cardinality.  cap < cardinality returns RB_ERANGE and writes nothing. */
+rb_status rb_to_u32(const rb_t *b, uint32_t *dst, int dst_on_device, uint64_t cap, uint64_t *n_out,
+                    void *stream);
+
+/* Cardinality (sum of container cardinalities; Sec. 5 "Fast counts"). */
+rb_status rb_cardinality(const rb_t *b, uint64_t *out);
+
+/* Number of containers and the size of the exported payload (array 2c B,
+ * bitset 8192 B, run 4r B per container). */
+rb_status rb_info(const rb_t *b, uint32_t *n_containers, uint64_t *payload_bytes);
+
+/* Copy the canonical layout to host arrays: keys[n] (u16), types[n] (u8,
+ * RB_TYPE_*), cards[n] (u32), offs[n + 1] (u64, byte offsets into payload),
+ * and payload (array: ascending u16; bitset: 1024 little-endian u64 words,
+ * bit v & 63 of word v >> 6; runs: (start, length - 1) u16 pairs, Sec. 1 and
+ * Fig. 1).  payload_cap below the size from rb_info returns RB_ERANGE. */
+rb_status rb_export_layout(const rb_t *b, uint16_t *keys, uint8_t *types, uint32_t *cards,
+                           uint64_t *offs, uint8_t *payload, uint64_t payload_cap, void *stream);
+
+/* Release a handle (NULL is ignored).  Device memory shared with other
+ * handles of the same batch is returned when its last handle is freed. */
+void rb_free(rb_t *b);
+
+/* ------------------------------------------------------------- pairwise */
+
+/* out = a op b as a new canonical bitmap (Sec. 1 set operations; Sec. 5
+ * materialised pairwise operations).  Key merge, per-container-pair work and
+ * canonical compaction all run on the device. */
+rb_status rb_apply(rb_op op, const rb_t *a, const rb_t *b, rb_t **out, void *stream);
+rb_status rb_and(const rb_t *a, const rb_t *b, rb_t **out, void *stream);
+rb_status rb_or(const rb_t *a, const rb_t *b, rb_t **out, void *stream);
+rb_status rb_andnot(const rb_t *a, const rb_t *b, rb_t **out, void *stream);
+rb_status rb_xor(const rb_t *a, const rb_t *b, rb_t **out, void *stream);
+
+/* |a op b| without materialising the result.  Sec. 5 "Fast counts": only
+ * |a n b| is computed on the device; |a u b| = |a| + |b| - |a n b|,
+ * |a \ b| = |a| - |a n b|, |a xor b| = |a| + |b| - 2 |a n b|. */
+rb_status rb_apply_cardinality(rb_op op, const rb_t *a, const rb_t *b, uint64_t *out, void *stream);
+rb_status rb_and_cardinality(const rb_t *a, const rb_t *b, uint64_t *out, void *stream);
+rb_status rb_or_cardinality(const rb_t *a, const rb_t *b, uint64_t *out, void *stream);
+rb_status rb_andnot_cardinality(const rb_t *a, const rb_t *b, uint64_t *out, void *stream);
+rb_status rb_xor_cardinality(const rb_t *a, const rb_t *b, uint64_t *out, void *stream);
+
+/* Jaccard index |a n b| / |a u b| (Sec. 5 "Fast counts").  inter and uni
+ * (either may be NULL) receive the two integers; *out is their quotient as a
+ * correctly rounded double, and 0.0 when both sets are empty. */
+rb_status rb_jaccard(const rb_t *a, const rb_t *b, double *out, uint64_t *inter, uint64_t *uni,
+                     void *stream);
+
+/* -------------------------------------------------------------- batches */
+
+/* One query of a batch: op (rb_op), indexes a and b into the pool, flags. */
+typedef struct {
+    uint32_t op;
+    uint32_t a;
+    uint32_t b;
+    uint32_t flags;
+} rb_query;
+#define RB_Q_COUNT_ONLY 1u   /* return |a op b| only; no bitmap */
+
+/* Run nq pairwise queries over a pool of bitmaps in one persistent,
+ * work-stealing launch over container pairs (no paper counterpart: the
+ * batching pattern of this library).  outs[i] receives the result bitmap of a
+ * materialising query and NULL for a count-only one (outs may be NULL when
+ * every query is count-only); counts[i] (counts may be NULL) receives the
+ * result's cardinality.  Results are identical to nq separate rb_apply /
+ * rb_apply_cardinality calls. */
+rb_status rb_batch_op(const rb_t *const *pool, uint32_t pool_n, const rb_query *q, uint64_t nq,
+                      rb_t **outs, uint64_t *counts, void *stream);
+
+/* Jaccard indexes of n pairs (a[i], b[i]) of the pool, count-only. */
+rb_status rb_batch_jaccard(const rb_t *const *pool, uint32_t pool_n, const uint32_t *a,
+                           const uint32_t *b, uint64_t n, double *jac, uint64_t *inter,
+                           uint64_t *uni, void *stream);
+
+/* A reusable batch: the host-side preparation (key counts, slot and tile
+ * prefix sums, device tables) is done once; each rb_plan_run replays the
+ * launch sequence as a CUDA graph and returns fresh result handles.  The
+ * pool's bitmaps must outlive the plan. */
+typedef struct rb_plan rb_plan_t;
+rb_status rb_plan_create(const rb_t *const *pool, uint32_t pool_n, const rb_query *q, uint64_t nq,
+                         void *stream, rb_plan_t **out);
+rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream);
+/* Time of the last run's container-pair kernel (device milliseconds), the
+ * algorithmic bytes it moved, and the bytes of the arena it wrote. */
+rb_status rb_plan_stats(const rb_plan_t *p, double *kernel_ms, uint64_t *alg_bytes,
+                        uint64_t *out_bytes);
+void rb_plan_free(rb_plan_t *p);
+
+/* ------------------------------------------------------------ schedules */
+
+/* Launch schedule of the container-pair kernels: warps per CTA (2, 4 or 8),
+ * CTAs per SM, and the largest container pair, in intervals (array values or
+ * runs on both sides), that one lane processes alone; bigger pairs are
+ * processed by a whole warp. */
+typedef struct {
+    uint32_t warps_per_cta;
+    uint32_t ctas_per_sm;
+    uint32_t small_intervals;
+    uint32_t reserved;
+} rb_schedule;
+rb_status rb_set_schedule(const rb_schedule *s);
+rb_status rb_get_schedule(rb_schedule *s);
+
+/* Time every candidate schedule on the plan (reps runs each, CUDA events),
+ * install the fastest as the current schedule and return it. */
+rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *best,
+                      double *best_ms);
+
+/* ------------------------------------------------------------ multi-way */
+
+/* out = in[0] op in[1] op ... op in[k-1] for op RB_AND or RB_OR (Sec. 5 "Wide
+ * unions": the union of many sets; the intersection likewise), computed key
+ * by key in one pass: each output key folds its k containers once.  card (may
+ * be NULL) receives the result's cardinality.  out may be NULL for a
+ * count-only evaluation.  k == 0 gives the empty set. */
+rb_status rb_multi_op(rb_op op, const rb_t *const *in, uint32_t k, rb_t **out, uint64_t *card,
+                      void *stream);
+
+/* -------------------------------------------------------------- serving */
+
+/* A serving loop over a device-resident index (no paper counterpart).
+ * Requests are multi-way AND / OR queries over index members, materialised
+ * or count-only.  A host thread admits queued requests in arrival order
+ * while a stream slot is free (max_inflight_batches) and the memory budget
+ * covers each request's worst-case result bytes, batches them (at most
+ * max_batch per batch), and launches each batch on its own stream, so
+ * batches overlap on the device while new requests keep arriving
+ * (continuous batching).  Result memory is charged to mem_budget until the
+ * caller frees the result; the loop allocates it with cudaMallocAsync from
+ * its own thread.  rb_server_destroy completes batches in flight and fails
+ * requests never admitted with RB_EBUSY. */
+#define RB_SERVE_MAX_K 8
+typedef struct {
+    uint32_t op;            /* RB_AND or RB_OR */
+    uint32_t k;             /* 1 .. RB_SERVE_MAX_K members */
+    uint32_t count_only;    /* non-zero: cardinality only */
+    uint32_t members[RB_SERVE_MAX_K];
+} rb_request;
+
+typedef struct rb_server rb_server_t;
+rb_status rb_server_create(const rb_t *const *index, uint32_t n, uint64_t mem_budget,
+                           uint32_t max_inflight_batches, uint32_t max_batch,
+                           rb_server_t **out);
+/* Queue a request; returns at once with a ticket.  RB_EBUSY if the request
+ * alone exceeds the whole budget. */
+rb_status rb_server_submit(rb_server_t *s, const rb_request *r, uint64_t *ticket);
+/* Wait (at most timeout_ms) for a ticket.  *out (may be NULL) receives the
+ * result bitmap of a materialising request (caller frees it); *card its
+ * cardinality; *latency_s the time from submit to completion on the device.
+ * RB_ETIMEOUT if it is not done in time (the ticket stays valid). */
+rb_status rb_server_wait(rb_server_t *s, uint64_t ticket, int timeout_ms, rb_t **out,
+                         uint64_t *card, double *latency_s);
+/* Counters: completed requests, launched batches, peak requests in flight. */
+rb_status rb_server_stats(rb_server_t *s, uint64_t *completed, uint64_t *batches,
+                          uint64_t *peak_inflight);
+void rb_server_destroy(rb_server_t *s);
+
+/* ----------------------------------------------------------------- misc */
+
+/* Message describing the calling thread's last error ("" if none). */
+const char *rb_last_error(void);
+
+/* Library version string. */
+const char *rb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RB_H */

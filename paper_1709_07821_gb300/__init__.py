@@ -1,0 +1,432 @@
+"""Python binding of librb.so, the GB300 Roaring bitmap library (include/rb.h).
+
+Argument marshalling only: every step of every operation runs in the CUDA
+kernels behind the C ABI.  PyTorch supplies device memory (its caching
+allocator is installed as the library's allocator) and the current stream.
+If librb.so is missing the first call raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librb.so")
+_lib = None
+_keep = []          # ctypes callbacks that must stay alive
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EBUSY, ERANGE = range(7)
+AND, OR, ANDNOT, XOR = 0, 1, 2, 3
+ARRAY, BITSET, RUN = 0, 1, 2
+Q_COUNT_ONLY = 1
+SERVE_MAX_K = 8
+
+
+class RoaringError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rb status {status}: {msg}")
+        self.status = status
+
+
+class Query(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint32), ("a", ctypes.c_uint32), ("b", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("small_intervals", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"warps_per_cta": self.warps_per_cta, "ctas_per_sm": self.ctas_per_sm,
+                "small_intervals": self.small_intervals}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint32), ("k", ctypes.c_uint32), ("count_only", ctypes.c_uint32),
+                ("members", ctypes.c_uint32 * SERVE_MAX_K)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def build(force: bool = False) -> str:
+    """Compile librb.so in-tree for sm_103a (see _build.py)."""
+    from . import _build
+    return _build.build(force=force)
+
+
+def _sig(L):
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    pu64, pu32, pdbl = ctypes.POINTER(u64), ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_double)
+    pvp = ctypes.POINTER(vp)
+    spec = {
+        "rb_set_allocator": [ALLOC_FN, FREE_FN, vp],
+        "rb_from_sorted_u32": [vp, u64, i32, vp, pvp],
+        "rb_to_u32": [vp, vp, i32, u64, pu64, vp],
+        "rb_cardinality": [vp, pu64],
+        "rb_info": [vp, pu32, pu64],
+        "rb_export_layout": [vp, vp, vp, vp, vp, vp, u64, vp],
+        "rb_apply": [i32, vp, vp, pvp, vp],
+        "rb_and": [vp, vp, pvp, vp], "rb_or": [vp, vp, pvp, vp],
+        "rb_andnot": [vp, vp, pvp, vp], "rb_xor": [vp, vp, pvp, vp],
+        "rb_apply_cardinality": [i32, vp, vp, pu64, vp],
+        "rb_and_cardinality": [vp, vp, pu64, vp], "rb_or_cardinality": [vp, vp, pu64, vp],
+        "rb_andnot_cardinality": [vp, vp, pu64, vp], "rb_xor_cardinality": [vp, vp, pu64, vp],
+        "rb_jaccard": [vp, vp, pdbl, pu64, pu64, vp],
+        "rb_batch_op": [vp, u32, vp, u64, vp, vp, vp],
+        "rb_batch_jaccard": [vp, u32, vp, vp, u64, vp, vp, vp, vp],
+        "rb_plan_create": [vp, u32, vp, u64, vp, pvp],
+        "rb_plan_run": [vp, vp, vp, vp],
+        "rb_plan_stats": [vp, pdbl, pu64, pu64],
+        "rb_set_schedule": [ctypes.POINTER(Schedule)],
+        "rb_get_schedule": [ctypes.POINTER(Schedule)],
+        "rb_autotune": [vp, u32, vp, ctypes.POINTER(Schedule), pdbl],
+        "rb_multi_op": [i32, vp, u32, pvp, pu64, vp],
+        "rb_server_create": [vp, u32, u64, u32, u32, pvp],
+        "rb_server_submit": [vp, ctypes.POINTER(Request), pu64],
+        "rb_server_wait": [vp, u64, i32, pvp, pu64, pdbl],
+        "rb_server_stats": [vp, pu64, pu64, pu64],
+    }
+    for name, args in spec.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    for name in ("rb_free", "rb_plan_free", "rb_server_destroy"):
+        getattr(L, name).argtypes = [vp]
+        getattr(L, name).restype = None
+    L.rb_last_error.restype = ctypes.c_char_p
+    L.rb_version.restype = ctypes.c_char_p
+
+
+def _install_torch_allocator(L):
+    import torch
+
+    if not torch.cuda.is_available():
+        return
+
+    @ALLOC_FN
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    @FREE_FN
+    def _free(ptr, nbytes, stream, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    _keep.extend([_alloc, _free])
+    _check(L.rb_set_allocator(_alloc, _free, None))
+
+
+def lib():
+    """The loaded librb.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1709_07821_gb300.build() "
+                               "(nvcc, sm_103a). There is no CPU fallback.")
+        L = ctypes.CDLL(LIB_PATH)
+        _sig(L)
+        _lib = L
+        _install_torch_allocator(L)
+    return _lib
+
+
+def _check(st):
+    if st != OK:
+        raise RoaringError(st, _lib.rb_last_error().decode() if _lib else "")
+
+
+def _stream(stream=None):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def version() -> str:
+    return lib().rb_version().decode()
+
+
+class Bitmap:
+    """Handle on a device-resident canonical Roaring bitmap."""
+
+    __slots__ = ("_h",)
+
+    def __init__(self, handle: int):
+        self._h = handle
+
+    # construction -----------------------------------------------------------
+    @classmethod
+    def from_sorted(cls, values, stream=None) -> "Bitmap":
+        """From strictly increasing uint32 values: a numpy array (host) or a
+        torch CUDA tensor of 4-byte integers (device)."""
+        L = lib()
+        h = ctypes.c_void_p()
+        if hasattr(values, "is_cuda") and values.is_cuda:
+            t = values.contiguous()
+            if t.element_size() != 4:
+                raise TypeError("device values must be 4-byte integers")
+            _check(L.rb_from_sorted_u32(ctypes.c_void_p(t.data_ptr()), t.numel(), 1, _stream(stream),
+                                        ctypes.byref(h)))
+        else:
+            v = np.ascontiguousarray(values, dtype=np.uint32)
+            _check(L.rb_from_sorted_u32(v.ctypes.data if v.size else None, v.size, 0, _stream(stream),
+                                        ctypes.byref(h)))
+        return cls(h.value)
+
+    # inspection -------------------------------------------------------------
+    @property
+    def card(self) -> int:
+        c = ctypes.c_uint64()
+        _check(lib().rb_cardinality(self._h, ctypes.byref(c)))
+        return c.value
+
+    def __len__(self):
+        return self.card
+
+    @property
+    def n_containers(self) -> int:
+        n = ctypes.c_uint32()
+        _check(lib().rb_info(self._h, ctypes.byref(n), None))
+        return n.value
+
+    def payload_bytes(self) -> int:
+        p = ctypes.c_uint64()
+        _check(lib().rb_info(self._h, None, ctypes.byref(p)))
+        return p.value
+
+    def to_numpy(self, stream=None) -> np.ndarray:
+        n = self.card
+        out = np.empty(n, np.uint32)
+        got = ctypes.c_uint64()
+        _check(lib().rb_to_u32(self._h, out.ctypes.data if n else None, 0, n, ctypes.byref(got), _stream(stream)))
+        return out
+
+    def to_tensor(self, stream=None):
+        import torch
+        n = self.card
+        out = torch.empty(n, dtype=torch.int32, device="cuda")
+        got = ctypes.c_uint64()
+        _check(lib().rb_to_u32(self._h, ctypes.c_void_p(out.data_ptr()) if n else None, 1, n, ctypes.byref(got),
+                               _stream(stream)))
+        return out
+
+    def layout(self, stream=None) -> dict:
+        """keys u16, types u8, cards u32, offs u64[n+1], payload u8 (canonical)."""
+        L = lib()
+        n = ctypes.c_uint32()
+        p = ctypes.c_uint64()
+        _check(L.rb_info(self._h, ctypes.byref(n), ctypes.byref(p)))
+        n, p = n.value, p.value
+        keys = np.empty(n, np.uint16)
+        types = np.empty(n, np.uint8)
+        cards = np.empty(n, np.uint32)
+        offs = np.empty(n + 1, np.uint64)
+        payload = np.empty(p, np.uint8)
+        _check(L.rb_export_layout(self._h, keys.ctypes.data, types.ctypes.data, cards.ctypes.data, offs.ctypes.data,
+                                  payload.ctypes.data if p else None, p, _stream(stream)))
+        return {"keys": keys, "types": types, "cards": cards, "offs": offs, "payload": payload}
+
+    # operations -------------------------------------------------------------
+    def op(self, op: int, other: "Bitmap", stream=None) -> "Bitmap":
+        h = ctypes.c_void_p()
+        _check(lib().rb_apply(op, self._h, other._h, ctypes.byref(h), _stream(stream)))
+        return Bitmap(h.value)
+
+    def op_card(self, op: int, other: "Bitmap", stream=None) -> int:
+        c = ctypes.c_uint64()
+        _check(lib().rb_apply_cardinality(op, self._h, other._h, ctypes.byref(c), _stream(stream)))
+        return c.value
+
+    def jaccard(self, other: "Bitmap", stream=None):
+        j, i, u = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().rb_jaccard(self._h, other._h, ctypes.byref(j), ctypes.byref(i), ctypes.byref(u),
+                                _stream(stream)))
+        return j.value, i.value, u.value
+
+    def __and__(self, o):
+        return self.op(AND, o)
+
+    def __or__(self, o):
+        return self.op(OR, o)
+
+    def __sub__(self, o):
+        return self.op(ANDNOT, o)
+
+    def __xor__(self, o):
+        return self.op(XOR, o)
+
+    # lifetime ---------------------------------------------------------------
+    def free(self):
+        if self._h:
+            if _lib is not None:
+                _lib.rb_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _handles(bitmaps):
+    return (ctypes.c_void_p * max(1, len(bitmaps)))(*[b._h for b in bitmaps])
+
+
+def _queries(ops, a, b, flags=None):
+    n = len(ops)
+    q = (Query * max(1, n))()
+    arr = np.frombuffer(q, dtype=np.uint32, count=4 * n).reshape(n, 4) if n else None
+    if n:
+        arr[:, 0] = ops
+        arr[:, 1] = a
+        arr[:, 2] = b
+        arr[:, 3] = 0 if flags is None else flags
+    return q
+
+
+def batch_op(pool, ops, a, b, flags=None, stream=None):
+    """Run len(ops) pairwise queries over `pool` in one launch.  Returns
+    (bitmaps, counts): bitmaps[i] is None for count-only queries."""
+    n = len(ops)
+    q = _queries(ops, a, b, flags)
+    outs = (ctypes.c_void_p * max(1, n))()
+    counts = np.zeros(n, np.uint64)
+    _check(lib().rb_batch_op(_handles(pool), len(pool), q, n, outs, counts.ctypes.data if n else None,
+                             _stream(stream)))
+    return [Bitmap(outs[i]) if outs[i] else None for i in range(n)], counts
+
+
+def batch_jaccard(pool, a, b, stream=None):
+    a = np.ascontiguousarray(a, np.uint32)
+    b = np.ascontiguousarray(b, np.uint32)
+    n = len(a)
+    j = np.zeros(n, np.float64)
+    i = np.zeros(n, np.uint64)
+    u = np.zeros(n, np.uint64)
+    _check(lib().rb_batch_jaccard(_handles(pool), len(pool), a.ctypes.data, b.ctypes.data, n, j.ctypes.data,
+                                  i.ctypes.data, u.ctypes.data, _stream(stream)))
+    return j, i, u
+
+
+class Plan:
+    """A reusable batch: prepared once, replayed as a CUDA graph per run."""
+
+    def __init__(self, pool, ops, a, b, flags=None, stream=None):
+        self._pool = list(pool)
+        self.n = len(ops)
+        self._q = _queries(ops, a, b, flags)
+        h = ctypes.c_void_p()
+        _check(lib().rb_plan_create(_handles(self._pool), len(self._pool), self._q, self.n, _stream(stream),
+                                    ctypes.byref(h)))
+        self._h = h.value
+
+    def run(self, stream=None, want_bitmaps=True):
+        outs = (ctypes.c_void_p * max(1, self.n))()
+        counts = np.zeros(self.n, np.uint64)
+        _check(lib().rb_plan_run(self._h, outs, counts.ctypes.data if self.n else None, _stream(stream)))
+        bms = [Bitmap(outs[i]) if outs[i] else None for i in range(self.n)]
+        if not want_bitmaps:
+            for x in bms:
+                if x is not None:
+                    x.free()
+            bms = None
+        return bms, counts
+
+    def stats(self):
+        ms, alg, ob = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().rb_plan_stats(self._h, ctypes.byref(ms), ctypes.byref(alg), ctypes.byref(ob)))
+        return {"kernel_ms": ms.value, "alg_bytes": alg.value, "out_bytes": ob.value}
+
+    def autotune(self, reps=2, stream=None):
+        s = Schedule()
+        ms = ctypes.c_double()
+        _check(lib().rb_autotune(self._h, reps, _stream(stream), ctypes.byref(s), ctypes.byref(ms)))
+        return s.as_dict(), ms.value
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().rb_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def get_schedule() -> dict:
+    s = Schedule()
+    _check(lib().rb_get_schedule(ctypes.byref(s)))
+    return s.as_dict()
+
+
+def set_schedule(warps_per_cta: int, ctas_per_sm: int, small_intervals: int):
+    s = Schedule(warps_per_cta, ctas_per_sm, small_intervals, 0)
+    _check(lib().rb_set_schedule(ctypes.byref(s)))
+
+
+def multi_op(op: int, inputs, count_only: bool = False, stream=None):
+    """k-way AND / OR.  Returns (bitmap or None, cardinality)."""
+    h = ctypes.c_void_p()
+    c = ctypes.c_uint64()
+    _check(lib().rb_multi_op(op, _handles(inputs), len(inputs), None if count_only else ctypes.byref(h),
+                             ctypes.byref(c), _stream(stream)))
+    return (None if count_only else Bitmap(h.value)), c.value
+
+
+class Server:
+    """Continuous-batching serving loop over a device-resident index."""
+
+    def __init__(self, index, mem_budget: int, max_inflight_batches: int = 4, max_batch: int = 256):
+        self._index = list(index)
+        h = ctypes.c_void_p()
+        _check(lib().rb_server_create(_handles(self._index), len(self._index), mem_budget, max_inflight_batches,
+                                      max_batch, ctypes.byref(h)))
+        self._h = h.value
+
+    def submit(self, op: int, members, count_only: bool = False) -> int:
+        r = Request()
+        r.op = op
+        r.k = len(members)
+        r.count_only = 1 if count_only else 0
+        for i, m in enumerate(members):
+            r.members[i] = int(m)
+        t = ctypes.c_uint64()
+        _check(lib().rb_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000, want_bitmap: bool = True):
+        h = ctypes.c_void_p()
+        c = ctypes.c_uint64()
+        lat = ctypes.c_double()
+        _check(lib().rb_server_wait(self._h, ticket, timeout_ms, ctypes.byref(h) if want_bitmap else None,
+                                    ctypes.byref(c), ctypes.byref(lat)))
+        return (Bitmap(h.value) if h.value else None), c.value, lat.value
+
+    def stats(self):
+        c, b, p = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().rb_server_stats(self._h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(p)))
+        return {"completed": c.value, "batches": b.value, "peak_inflight": p.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

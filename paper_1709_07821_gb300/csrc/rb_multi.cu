@@ -1,0 +1,682 @@
+// rb_multi.cu - k-way AND / OR over many bitmaps in one pass (Sec. 5 "Wide
+// unions" computes the union of many sets; this engine folds the k
+// containers of each output key once, instead of a sequential fold).
+//
+// Slots.  AND: the keys of the member with the fewest keys (a key survives
+// only if every member has it).  OR: the keys of every member; a slot owns
+// its key if no earlier member has it, and the key's output position is its
+// rank among the distinct keys, read from a per-query 65536-bit presence
+// bitmap and the prefix of its word popcounts.
+#include <algorithm>
+#include <cstring>
+
+#include "rb_device.cuh"
+#include "rb_multi.h"
+
+using namespace rbi;
+using namespace rbd;
+
+namespace {
+
+constexpr uint32_t KIND_NONE = 0, KIND_EMPTY = 1, KIND_FOLD = 2;
+
+struct MultiDev {
+    uint32_t op, count_only, k, driver;
+    uint32_t mbase, obase, pres_idx, n_slots;
+    unsigned long long slot_base;
+};
+
+struct MStats {
+    unsigned long long card, words, in_bytes;
+    unsigned int n_out, n_pos, nbits, pad;
+};
+
+struct MState {
+    uint8_t *arena;
+    uint16_t *keys;
+    uint64_t *descs;
+    unsigned long long words_off, words_cap, bits_off, bits_cap;
+    unsigned long long words_used, bits_used, work;
+    unsigned int status, pad;
+};
+
+struct MParams {
+    const BmView *pool;
+    const MultiDev *qs;
+    const uint32_t *members;
+    const uint32_t *moff;
+    const unsigned long long *tile_base;
+    const unsigned long long *pres;
+    const uint32_t *prefix;
+    MStats *stats;
+    MState *es;
+    unsigned long long n_tiles;
+    uint32_t n_q, pad;
+};
+
+__device__ __forceinline__ bool find_key(const BmView &V, uint32_t key, uint32_t &j) {
+    j = lower_bound16(V.keys, V.n, key);
+    return j < V.n && __ldg(V.keys + j) == key;
+}
+
+// T0 = T0 op words, words a shared tile or a global bitset
+__device__ __forceinline__ void t_apply(uint64_t *T0, const uint64_t *w, uint32_t op, uint32_t lane) {
+    ulonglong2 *D = reinterpret_cast<ulonglong2 *>(T0);
+    const ulonglong2 *S = reinterpret_cast<const ulonglong2 *>(w);
+#pragma unroll 4
+    for (int k = 0; k < 16; k++) {
+        ulonglong2 a = D[32 * k + lane], b = S[32 * k + lane];
+        D[32 * k + lane] = make_ulonglong2(apply_op(op, a.x, b.x), apply_op(op, a.y, b.y));
+    }
+    __syncwarp();
+}
+
+// fold one container into the accumulator tile T0 (T1 is scratch)
+__device__ void fold_into(uint64_t *T0, uint64_t *T1, const CRef &x, uint32_t op, uint32_t lane) {
+    if (x.type == T_BITSET) {
+        t_apply(T0, reinterpret_cast<const uint64_t *>(x.p), op, lane);
+    } else if (x.type == T_ARRAY && op == OP_OR) {
+        t_or_array(T0, reinterpret_cast<const uint16_t *>(x.p), x.card, lane);
+        __syncwarp();
+    } else {
+        t_decode(T1, x, lane);
+        t_apply(T0, T1, op, lane);
+    }
+}
+
+__device__ uint64_t alloc_w(MState *es, uint32_t bytes, uint32_t lane) {
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(&es->words_used, (unsigned long long)bytes);
+    old = __shfl_sync(FULL, old, 0);
+    if (old + bytes > es->words_cap) {
+        if (lane == 0) atomicOr(&es->status, 1u);
+        return ALLOC_FAIL;
+    }
+    return es->words_off + old;
+}
+__device__ uint64_t alloc_b(MState *es, uint32_t lane) {
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(&es->bits_used, 8192ull);
+    old = __shfl_sync(FULL, old, 0);
+    if (old + 8192ull > es->bits_cap) {
+        if (lane == 0) atomicOr(&es->status, 1u);
+        return ALLOC_FAIL;
+    }
+    return es->bits_off + old;
+}
+
+__device__ void multi_tile(const MParams &P, unsigned long long t, uint64_t *T0, uint64_t *T1, uint32_t lane) {
+    uint32_t lo = 0, hi = P.n_q;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (P.tile_base[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    const uint32_t q = lo;
+    const MultiDev qd = P.qs[q];
+    const uint32_t *mem = P.members + qd.mbase;
+    const uint32_t slot = (uint32_t)(t - P.tile_base[q]) * 32u + lane;
+    uint32_t kind = KIND_NONE, key = 0, pos = 0;
+    if (slot < qd.n_slots) {
+        if (qd.op == OP_AND) {
+            const BmView D = P.pool[mem[qd.driver]];
+            key = __ldg(D.keys + slot);
+            pos = slot;
+            kind = KIND_FOLD;
+            for (uint32_t i = 0; i < qd.k; i++) {
+                if (i == qd.driver) continue;
+                uint32_t j;
+                if (!find_key(P.pool[mem[i]], key, j)) { kind = KIND_EMPTY; break; }
+            }
+        } else {
+            const uint32_t *mo = P.moff + qd.obase;
+            uint32_t l = 0, h = qd.k;   // largest i with mo[i] <= slot
+            while (h - l > 1) {
+                uint32_t m = (l + h) >> 1;
+                if (mo[m] <= slot) l = m;
+                else h = m;
+            }
+            const BmView V = P.pool[mem[l]];
+            key = __ldg(V.keys + (slot - mo[l]));
+            bool owner = true;
+            for (uint32_t i = 0; i < l && owner; i++) {
+                uint32_t j;
+                if (find_key(P.pool[mem[i]], key, j)) owner = false;
+            }
+            if (owner) {
+                kind = KIND_FOLD;
+                const unsigned long long *pr = P.pres + (size_t)qd.pres_idx * 1024;
+                const uint32_t w = key >> 6;
+                pos = P.prefix[(size_t)qd.pres_idx * 1024 + w] + __popcll(pr[w] & ((1ull << (key & 63)) - 1ull));
+            }
+        }
+    }
+    MState *es = P.es;
+    uint16_t *OKEY = es->keys + qd.slot_base;
+    uint64_t *ODESC = es->descs + qd.slot_base;
+    if (kind == KIND_EMPTY && !qd.count_only) {
+        ODESC[pos] = DESC_EMPTY;
+        OKEY[pos] = (uint16_t)key;
+    }
+    unsigned long long card_acc = 0, words_acc = 0, in_acc = 0;
+    uint32_t bits_acc = 0;
+    uint32_t lm = __ballot_sync(FULL, kind == KIND_FOLD);
+    while (lm) {
+        const int src = __ffs(lm) - 1;
+        lm &= lm - 1;
+        const uint32_t k_key = __shfl_sync(FULL, key, src), k_pos = __shfl_sync(FULL, pos, src);
+        // fold the k containers of this key
+        if (qd.op == OP_AND) {
+            const BmView D = P.pool[mem[qd.driver]];
+            uint32_t j;
+            find_key(D, k_key, j);
+            const uint64_t d0 = __ldg(D.descs + j);
+            t_decode(T0, cref(D.base, d0), lane);
+            in_acc += in_payload_bytes(d0) + 10;
+            for (uint32_t i = 0; i < qd.k; i++) {
+                if (i == qd.driver) continue;
+                const BmView V = P.pool[mem[i]];
+                find_key(V, k_key, j);
+                const uint64_t d = __ldg(V.descs + j);
+                in_acc += in_payload_bytes(d) + 10;
+                fold_into(T0, T1, cref(V.base, d), OP_AND, lane);
+            }
+        } else {
+            t_zero(T0, lane);
+            __syncwarp();
+            for (uint32_t i = 0; i < qd.k; i++) {
+                const BmView V = P.pool[mem[i]];
+                uint32_t j;
+                if (!find_key(V, k_key, j)) continue;
+                const uint64_t d = __ldg(V.descs + j);
+                in_acc += in_payload_bytes(d) + 10;
+                fold_into(T0, T1, cref(V.base, d), OP_OR, lane);
+            }
+        }
+        uint32_t c, r;
+        t_combine<false>(nullptr, T0, T0, OP_OR, c, r, lane);
+        __syncwarp();
+        if (qd.count_only) {
+            card_acc += c;
+            continue;
+        }
+        uint64_t desc = DESC_EMPTY;
+        if (c) {
+            const uint32_t ty = canon_type(c, r);
+            if (ty == T_BITSET) {
+                const uint64_t off = alloc_b(es, lane);
+                if (off != ALLOC_FAIL) {
+                    t_emit_bitset(T0, reinterpret_cast<uint64_t *>(es->arena + off), lane);
+                    desc = mk_desc(c, ty, 0, off);
+                }
+            } else {
+                const uint32_t bytes = word_alloc_bytes(ty, c, r);
+                const uint64_t off = alloc_w(es, bytes, lane);
+                if (off != ALLOC_FAIL) {
+                    if (ty == T_ARRAY) {
+                        t_emit_array(T0, reinterpret_cast<uint16_t *>(es->arena + off), lane);
+                    } else {
+                        uint16_t *S = reinterpret_cast<uint16_t *>(T1);
+                        t_emit_runs(T0, S, S + 2048, reinterpret_cast<uint32_t *>(es->arena + off), r, lane);
+                    }
+                    desc = mk_desc(c, ty, ty == T_RUN ? r : 0, off);
+                }
+            }
+        }
+        if (lane == 0) {
+            ODESC[k_pos] = desc;
+            OKEY[k_pos] = (uint16_t)k_key;
+            if (desc != DESC_EMPTY) {
+                card_acc += c;
+                if (d_type(desc) == T_BITSET) bits_acc++;
+                else words_acc += word_alloc_bytes(d_type(desc), c, r);
+            }
+        }
+        __syncwarp();
+    }
+    // per lane accumulators are only on lane 0 except in_acc/card (uniform)
+    if (lane == 0) {
+        MStats *S = P.stats + q;
+        if (card_acc) atomicAdd(&S->card, card_acc);
+        if (words_acc) atomicAdd(&S->words, words_acc);
+        if (bits_acc) atomicAdd(&S->nbits, bits_acc);
+        if (in_acc) atomicAdd(&S->in_bytes, in_acc);
+    }
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) k_multi(MParams P) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *T0 = smem + (size_t)warp * 2048;
+    uint64_t *T1 = T0 + 1024;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(&P.es->work, 1ull);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= P.n_tiles) break;
+        multi_tile(P, t, T0, T1, lane);
+    }
+}
+
+// presence bits of every key of every member of every OR query
+__global__ void k_presence(const BmView *pool, const MultiDev *qs, const uint32_t *members, const uint32_t *items,
+                           uint32_t n_items, unsigned long long *pres) {
+    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const uint32_t q = items[2 * it], i = items[2 * it + 1];
+        const MultiDev qd = qs[q];
+        const BmView V = pool[members[qd.mbase + i]];
+        unsigned long long *pr = pres + (size_t)qd.pres_idx * 1024;
+        for (uint32_t j = threadIdx.x; j < V.n; j += blockDim.x) {
+            const uint32_t key = __ldg(V.keys + j);
+            atomicOr(pr + (key >> 6), 1ull << (key & 63));
+        }
+    }
+}
+
+// exclusive prefix of the word popcounts of each OR query's presence bitmap
+__global__ void __launch_bounds__(1024) k_rank(const MultiDev *qs, const uint32_t *or_q, uint32_t n_or,
+                                               const unsigned long long *pres, uint32_t *prefix, MStats *stats) {
+    __shared__ uint32_t s[32];
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (uint32_t x = blockIdx.x; x < n_or; x += gridDim.x) {
+        const uint32_t q = or_q[x];
+        const uint32_t pi = qs[q].pres_idx;
+        const uint32_t c = __popcll(pres[(size_t)pi * 1024 + t]);
+        const uint32_t inc = warp_incl(c, lane);
+        if (lane == 31) s[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t v = s[lane], vi = warp_incl(v, lane);
+            s[lane] = vi - v;
+            if (lane == 31) stats[q].n_pos = vi;
+        }
+        __syncthreads();
+        prefix[(size_t)pi * 1024 + t] = s[warp] + inc - c;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(512) k_mcompact(const MultiDev *qs, uint32_t n_q, MStats *stats, const MState *es) {
+    __shared__ uint32_t s_w[16];
+    __shared__ uint32_t s_tot;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (uint32_t q = blockIdx.x; q < n_q; q += gridDim.x) {
+        const MultiDev qd = qs[q];
+        if (qd.count_only) continue;
+        const uint32_t n = qd.op == OP_OR ? stats[q].n_pos : qd.n_slots;
+        uint64_t *D = es->descs + qd.slot_base;
+        uint16_t *K = es->keys + qd.slot_base;
+        uint32_t out = 0;
+        for (uint32_t c0 = 0; c0 < n; c0 += blockDim.x) {
+            const uint32_t i = c0 + tid;
+            const uint64_t d = i < n ? D[i] : DESC_EMPTY;
+            const uint16_t k = i < n ? K[i] : 0;
+            const uint32_t f = d != DESC_EMPTY;
+            const uint32_t m = __ballot_sync(FULL, f);
+            if (lane == 0) s_w[warp] = __popc(m);
+            __syncthreads();
+            if (warp == 0) {
+                const uint32_t v = lane < nw ? s_w[lane] : 0, inc = warp_incl(v, lane);
+                if (lane < nw) s_w[lane] = inc - v;
+                if (lane == 31) s_tot = inc;
+            }
+            __syncthreads();
+            if (f) {
+                const uint32_t at = out + s_w[warp] + __popc(m & lanemask_lt(lane));
+                D[at] = d;
+                K[at] = k;
+            }
+            out += s_tot;
+            __syncthreads();
+        }
+        if (tid == 0) stats[q].n_out = out;
+    }
+}
+
+}  // namespace
+
+namespace rbi {
+
+struct MultiBatch {
+    std::vector<const rb *> pool;
+    std::vector<MultiDev> qd;
+    std::vector<uint32_t> or_q;
+    uint64_t total_slots = 0, total_tiles = 0, words_cap = 0, bits_cap = 0;
+    uint32_t n_or = 0, n_items = 0;
+    bool any_mat = false;
+    const BmView *d_pool = nullptr;
+    uint8_t *tables = nullptr;
+    uint64_t tables_bytes = 0;
+    MultiDev *d_qs = nullptr;
+    uint32_t *d_members = nullptr, *d_moff = nullptr, *d_items = nullptr, *d_orq = nullptr, *d_prefix = nullptr;
+    unsigned long long *d_tb = nullptr, *d_pres = nullptr;
+    MStats *d_stats = nullptr;
+    MState *d_es = nullptr;
+    MStats *h_stats = nullptr;
+    MState *h_es = nullptr;
+    uint8_t *hpin = nullptr;
+    bool native = false;
+    uint64_t o_keys = 0, o_words = 0, o_bits = 0, arena_bytes = 0;
+};
+
+static void query_bounds(const rb *const *pool, const MultiQuery &x, uint64_t &ns, uint64_t &wcap, uint64_t &bcap) {
+    uint64_t sum_n = 0, sum_card = 0, min_card = ~0ull, nmin = ~0ull;
+    for (uint32_t m : x.members) {
+        const rb *B = pool[m];
+        sum_n += B->n;
+        sum_card += B->card;
+        min_card = std::min(min_card, B->card);
+        nmin = std::min<uint64_t>(nmin, B->n);
+    }
+    if (x.members.empty()) { nmin = 0; min_card = 0; }
+    // a canonical container is at most 8192 bytes and at most twice its
+    // cardinality (+ 4 bytes of rounding); a bitset needs more than 4096 values
+    if (x.op == OP_AND) {
+        ns = nmin;
+        wcap = std::min<uint64_t>(8192ull * ns, 2 * min_card + 4 * ns);
+        bcap = 8192ull * std::min<uint64_t>(ns, min_card / 4097 + 1);
+    } else {
+        ns = sum_n;
+        wcap = std::min<uint64_t>(8192ull * ns, 2 * sum_card + 4 * ns);
+        bcap = 8192ull * std::min<uint64_t>(ns, sum_card / 4097 + 1);
+    }
+}
+
+uint64_t multi_query_bound(const rb *const *pool, const MultiQuery &q) {
+    if (q.count_only) return 0;
+    uint64_t ns, w, b;
+    query_bounds(pool, q, ns, w, b);
+    return 10 * ns + w + b + 1024;
+}
+
+rb_status multi_prepare(const rb *const *pool, const BmView *d_pool, uint32_t pool_n, const std::vector<MultiQuery> &qs,
+                        cudaStream_t s, MultiBatch **out, uint64_t *arena_bytes, PinnedBuf *stage, bool native) {
+    *out = nullptr;
+    MultiBatch *b = new MultiBatch;
+    b->pool.assign(pool, pool + pool_n);
+    b->d_pool = d_pool;
+    const uint32_t nq = (uint32_t)qs.size();
+    b->qd.resize(nq);
+    std::vector<uint32_t> members, moff, items;
+    std::vector<unsigned long long> tb(nq + 1);
+    uint64_t slots = 0, tiles = 0, wcap = 0, bcap = 0;
+    for (uint32_t q = 0; q < nq; q++) {
+        const MultiQuery &x = qs[q];
+        MultiDev &d = b->qd[q];
+        memset(&d, 0, sizeof d);
+        if (x.op != OP_AND && x.op != OP_OR) {
+            delete b;
+            return set_err(RB_EINVAL, "multi-way op must be AND or OR");
+        }
+        d.op = x.op;
+        d.count_only = x.count_only ? 1 : 0;
+        d.k = (uint32_t)x.members.size();
+        d.mbase = (uint32_t)members.size();
+        d.obase = (uint32_t)moff.size();
+        uint64_t ns = 0, nmin = ~0ull;
+        for (uint32_t i = 0; i < d.k; i++) {
+            const uint32_t m = x.members[i];
+            if (m >= pool_n || !pool[m]) {
+                delete b;
+                return set_err(RB_EINVAL, "multi-way member %u out of range", m);
+            }
+            members.push_back(m);
+            moff.push_back((uint32_t)ns);
+            const rb *B = pool[m];
+            ns += B->n;
+            if (B->n < nmin) { nmin = B->n; d.driver = i; }
+        }
+        moff.push_back((uint32_t)ns);
+        uint64_t qw = 0, qb = 0;
+        query_bounds(pool, x, ns, qw, qb);
+        d.n_slots = (uint32_t)ns;
+        if (d.op == OP_OR && d.k) {
+            d.pres_idx = b->n_or++;
+            b->or_q.push_back(q);
+            for (uint32_t i = 0; i < d.k; i++) { items.push_back(q); items.push_back(i); }
+        }
+        if (!d.count_only) {
+            b->any_mat = true;
+            d.slot_base = slots;
+            slots += ns;
+            wcap += qw;
+            bcap += qb;
+        }
+        tb[q] = tiles;
+        tiles += (ns + 31) / 32;
+    }
+    tb[nq] = tiles;
+    b->n_items = (uint32_t)(items.size() / 2);
+    b->total_slots = slots;
+    b->total_tiles = tiles;
+    b->words_cap = wcap;
+    b->bits_cap = bcap;
+    b->o_keys = align_up(8 * slots, 256);
+    b->o_words = align_up(b->o_keys + 2 * slots, 256);
+    b->o_bits = align_up(b->o_words + wcap, 256);
+    b->arena_bytes = b->any_mat ? std::max<uint64_t>(256, b->o_bits + bcap) : 0;
+    if (b->arena_bytes >= MAX_OFFSET) {
+        delete b;
+        return set_err(RB_ERANGE, "multi-way results bound above the 128 GiB descriptor reach");
+    }
+    // device tables
+    const uint64_t o_qs = 0;
+    const uint64_t o_mem = align_up(o_qs + sizeof(MultiDev) * nq, 256);
+    const uint64_t o_moff = align_up(o_mem + 4 * members.size(), 256);
+    const uint64_t o_items = align_up(o_moff + 4 * moff.size(), 256);
+    const uint64_t o_orq = align_up(o_items + 4 * items.size(), 256);
+    const uint64_t o_tb = align_up(o_orq + 4 * b->or_q.size(), 256);
+    const uint64_t o_up = align_up(o_tb + 8ull * (nq + 1), 256);   // end of uploaded part
+    const uint64_t o_pres = o_up;
+    const uint64_t o_prefix = align_up(o_pres + 8192ull * b->n_or, 256);
+    const uint64_t o_stats = align_up(o_prefix + 4096ull * b->n_or, 256);
+    const uint64_t o_es = align_up(o_stats + sizeof(MStats) * nq, 256);
+    b->tables_bytes = o_es + 256;
+    b->native = native;
+    b->tables = (uint8_t *)(native ? dev_alloc_native(b->tables_bytes, s) : dev_alloc(b->tables_bytes, s));
+    if (!b->tables) { delete b; return RB_ENOMEM; }
+    b->d_qs = (MultiDev *)(b->tables + o_qs);
+    b->d_members = (uint32_t *)(b->tables + o_mem);
+    b->d_moff = (uint32_t *)(b->tables + o_moff);
+    b->d_items = (uint32_t *)(b->tables + o_items);
+    b->d_orq = (uint32_t *)(b->tables + o_orq);
+    b->d_tb = (unsigned long long *)(b->tables + o_tb);
+    b->d_pres = (unsigned long long *)(b->tables + o_pres);
+    b->d_prefix = (uint32_t *)(b->tables + o_prefix);
+    b->d_stats = (MStats *)(b->tables + o_stats);
+    b->d_es = (MState *)(b->tables + o_es);
+    std::vector<uint8_t> h(o_up, 0);
+    if (nq) memcpy(h.data() + o_qs, b->qd.data(), sizeof(MultiDev) * nq);
+    if (!members.empty()) memcpy(h.data() + o_mem, members.data(), 4 * members.size());
+    if (!moff.empty()) memcpy(h.data() + o_moff, moff.data(), 4 * moff.size());
+    if (!items.empty()) memcpy(h.data() + o_items, items.data(), 4 * items.size());
+    if (!b->or_q.empty()) memcpy(h.data() + o_orq, b->or_q.data(), 4 * b->or_q.size());
+    memcpy(h.data() + o_tb, tb.data(), 8ull * (nq + 1));
+    // pinned mirrors: the upload source must stay valid until the copy runs
+    uint8_t *hpin = nullptr;
+    const uint64_t pin_bytes =
+        align_up(o_up, 256) + align_up(sizeof(MStats) * std::max<uint32_t>(nq, 1), 256) + sizeof(MState) + 256;
+    cudaError_t e = cudaSuccess;
+    if (stage) {
+        if (stage->cap < pin_bytes) {
+            if (stage->p) cudaFreeHost(stage->p);
+            stage->p = nullptr;
+            stage->cap = 0;
+            e = cudaMallocHost((void **)&stage->p, align_up(pin_bytes, 1 << 20));
+            if (e == cudaSuccess) stage->cap = align_up(pin_bytes, 1 << 20);
+        }
+        hpin = stage->p;
+    } else {
+        e = cudaMallocHost((void **)&hpin, pin_bytes);
+    }
+    if (e != cudaSuccess) {
+        if (native) dev_free_native(b->tables, s);
+        else dev_free(b->tables, b->tables_bytes, s);
+        delete b;
+        return cuda_err(e, "multi-way pinned staging");
+    }
+    memcpy(hpin, h.data(), o_up);
+    b->hpin = stage ? nullptr : hpin;
+    b->h_stats = (MStats *)(hpin + align_up(o_up, 256));
+    b->h_es = (MState *)((uint8_t *)b->h_stats + align_up(sizeof(MStats) * std::max<uint32_t>(nq, 1), 256));
+    e = cudaMemcpyAsync(b->tables, hpin, o_up, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        if (!stage) cudaFreeHost(hpin);
+        if (native) dev_free_native(b->tables, s);
+        else dev_free(b->tables, b->tables_bytes, s);
+        delete b;
+        return cuda_err(e, "multi-way upload");
+    }
+    // the pinned block is released in multi_free, after the stream has run
+    *out = b;
+    *arena_bytes = b->arena_bytes;
+    return RB_OK;
+}
+
+template <int W>
+static void launch_multi_w(const MParams &P, int ctas, cudaStream_t s) {
+    static bool attr = false;
+    const int smem = W * 16384;
+    if (!attr) {
+        cudaFuncSetAttribute(k_multi<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    unsigned long long need = (P.n_tiles + W - 1) / W, cap = (unsigned long long)sm_count() * ctas;
+    unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min(need, cap));
+    k_multi<W><<<grid, W * 32, smem, s>>>(P);
+}
+
+rb_status multi_enqueue(MultiBatch *b, RbArena *arena, cudaStream_t s) {
+    clear_stale_error();
+    const uint32_t nq = (uint32_t)b->qd.size();
+    MState &h = *b->h_es;
+    memset(&h, 0, sizeof h);
+    if (b->any_mat) {
+        if (!arena || arena->bytes < b->arena_bytes) return set_err(RB_EINVAL, "multi-way arena too small");
+        h.arena = (uint8_t *)arena->ptr;
+        h.descs = (uint64_t *)arena->ptr;
+        h.keys = (uint16_t *)((uint8_t *)arena->ptr + b->o_keys);
+        h.words_off = b->o_words;
+        h.words_cap = b->words_cap;
+        h.bits_off = b->o_bits;
+        h.bits_cap = b->bits_cap;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_es, b->h_es, sizeof(MState), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nq) e = cudaMemsetAsync(b->d_stats, 0, sizeof(MStats) * nq, s);
+    if (e == cudaSuccess && b->n_or) e = cudaMemsetAsync(b->d_pres, 0, 8192ull * b->n_or, s);
+    if (e != cudaSuccess) return cuda_err(e, "multi-way enqueue");
+    if (b->n_or) {
+        const unsigned g1 = std::min<unsigned>(b->n_items, (unsigned)sm_count() * 16);
+        k_presence<<<std::max(1u, g1), 256, 0, s>>>(b->d_pool, b->d_qs, b->d_members, b->d_items, b->n_items, b->d_pres);
+        const unsigned g2 = std::min<unsigned>(b->n_or, (unsigned)sm_count() * 2);
+        k_rank<<<std::max(1u, g2), 1024, 0, s>>>(b->d_qs, b->d_orq, b->n_or, b->d_pres, b->d_prefix, b->d_stats);
+    }
+    MParams P;
+    P.pool = b->d_pool;
+    P.qs = b->d_qs;
+    P.members = b->d_members;
+    P.moff = b->d_moff;
+    P.tile_base = b->d_tb;
+    P.pres = b->d_pres;
+    P.prefix = b->d_prefix;
+    P.stats = b->d_stats;
+    P.es = b->d_es;
+    P.n_tiles = b->total_tiles;
+    P.n_q = nq;
+    P.pad = 0;
+    const rb_schedule sc = current_schedule();
+    if (b->total_tiles) {
+        switch (sc.warps_per_cta) {
+            case 2: launch_multi_w<2>(P, sc.ctas_per_sm, s); break;
+            case 8: launch_multi_w<8>(P, sc.ctas_per_sm, s); break;
+            default: launch_multi_w<4>(P, sc.ctas_per_sm, s); break;
+        }
+    }
+    if (b->any_mat) {
+        const unsigned g = std::max(1u, std::min<unsigned>(nq, (unsigned)sm_count() * 8));
+        k_mcompact<<<g, 512, 0, s>>>(b->d_qs, nq, b->d_stats, b->d_es);
+    }
+    e = cudaGetLastError();
+    if (e == cudaSuccess && nq) e = cudaMemcpyAsync(b->h_stats, b->d_stats, sizeof(MStats) * nq, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->h_es, b->d_es, sizeof(MState), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_err(e, "multi-way launch");
+    return RB_OK;
+}
+
+rb_status multi_finish(MultiBatch *b, RbArena *arena, rb_t **outs, uint64_t *cards) {
+    if (b->h_es->status & 1u) return set_err(RB_ENOMEM, "multi-way: result bound exceeded (internal error)");
+    for (size_t q = 0; q < b->qd.size(); q++) {
+        const MultiDev &d = b->qd[q];
+        const MStats &S = b->h_stats[q];
+        if (cards) cards[q] = S.card;
+        if (!outs) continue;
+        if (d.count_only) { outs[q] = nullptr; continue; }
+        rb *h = handle_new();
+        h->n = S.n_out;
+        h->card = S.card;
+        h->word_bytes = S.words;
+        h->n_bitsets = S.nbits;
+        h->base = (uint8_t *)arena->ptr;
+        h->descs = (uint64_t *)arena->ptr + d.slot_base;
+        h->keys = (uint16_t *)((uint8_t *)arena->ptr + b->o_keys) + d.slot_base;
+        h->arena = arena;
+        arena_ref(arena);
+        outs[q] = h;
+    }
+    return RB_OK;
+}
+
+void multi_free(MultiBatch *b, cudaStream_t s) {
+    if (!b) return;
+    if (b->tables) {
+        if (b->native) dev_free_native(b->tables, s);
+        else dev_free(b->tables, b->tables_bytes, s);
+    }
+    if (b->hpin) cudaFreeHost(b->hpin);
+    delete b;
+}
+
+}  // namespace rbi
+
+extern "C" rb_status rb_multi_op(rb_op op, const rb_t *const *in, uint32_t k, rb_t **out, uint64_t *card,
+                                 void *stream) {
+    if (out) *out = nullptr;
+    if (op != RB_AND && op != RB_OR) return set_err(RB_EINVAL, "rb_multi_op: op must be RB_AND or RB_OR");
+    if (k && !in) return set_err(RB_EINVAL, "rb_multi_op: NULL inputs");
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<BmView> hv(k);
+    for (uint32_t i = 0; i < k; i++) {
+        if (!in[i]) return set_err(RB_EINVAL, "rb_multi_op: in[%u] is NULL", i);
+        hv[i] = view_of(in[i]);
+    }
+    BmView *dv = (BmView *)dev_alloc(sizeof(BmView) * std::max<uint32_t>(k, 1), s);
+    if (!dv) return RB_ENOMEM;
+    cudaError_t e = k ? cudaMemcpyAsync(dv, hv.data(), sizeof(BmView) * k, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    if (e != cudaSuccess) { dev_free(dv, sizeof(BmView) * std::max<uint32_t>(k, 1), s); return cuda_err(e, "rb_multi_op"); }
+    MultiQuery mq;
+    mq.op = (uint32_t)op;
+    mq.count_only = out ? 0 : 1;
+    for (uint32_t i = 0; i < k; i++) mq.members.push_back(i);
+    std::vector<MultiQuery> qs(1, mq);
+    MultiBatch *b = nullptr;
+    uint64_t ab = 0;
+    rb_status st = multi_prepare(in, dv, k, qs, s, &b, &ab);
+    RbArena *a = nullptr;
+    if (st == RB_OK && ab) {
+        a = arena_new(ab, s);
+        if (!a) st = RB_ENOMEM;
+    }
+    if (st == RB_OK) st = multi_enqueue(b, a, s);
+    if (st == RB_OK) {
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_err(e, "rb_multi_op");
+    }
+    uint64_t c = 0;
+    if (st == RB_OK) st = multi_finish(b, a, out ? out : nullptr, &c);
+    if (st == RB_OK && card) *card = c;
+    if (b) multi_free(b, s);
+    arena_unref(a);
+    dev_free(dv, sizeof(BmView) * std::max<uint32_t>(k, 1), s);
+    return st;
+}

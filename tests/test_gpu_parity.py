@@ -1,0 +1,243 @@
+"""GPU parity: the CUDA path against the CPU oracle, bit for bit, as decoded
+uint32 sets and as canonical container layouts (keys, types, cardinalities,
+payload bytes).  All of this is integer work: the tolerance is zero."""
+import numpy as np
+import pytest
+
+from layout_tools import check_canonical
+
+pytestmark = pytest.mark.gpu
+
+OPS = (0, 1, 2, 3)
+NP_OPS = {0: np.intersect1d, 1: np.union1d, 2: lambda a, b: np.setdiff1d(a, b, assume_unique=True),
+          3: lambda a, b: np.setxor1d(a, b, assume_unique=True)}
+
+
+@pytest.fixture(scope="module")
+def rb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1709_07821_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_mod):
+    return oracle_mod
+
+
+def assert_layout_eq(got, exp, ctx=""):
+    for k in ("keys", "types", "cards", "offs", "payload"):
+        assert got[k].shape == exp[k].shape, (ctx, k, got[k].shape, exp[k].shape)
+        if not np.array_equal(got[k], exp[k]):
+            bad = np.nonzero(got[k] != exp[k])[0][:5]
+            raise AssertionError(f"{ctx}: {k} differs at {bad}: {got[k][bad]} vs {exp[k][bad]}")
+
+
+def chunk(rng, key, kind, size):
+    """Values of one chunk of a given container kind and size class."""
+    base = np.uint32(key) << np.uint32(16)
+    if kind == "array":
+        c = int(rng.integers(1, 12)) if size == "small" else int(rng.integers(300, 4097))
+        v = rng.choice(65536, size=c, replace=False)
+    elif kind == "bitset":
+        c = int(rng.integers(4097, 40000))
+        v = rng.choice(65536, size=c, replace=False)
+    else:
+        nr = int(rng.integers(1, 10)) if size == "small" else int(rng.integers(40, 600))
+        starts = np.sort(rng.choice(65536 // 32, size=nr, replace=False)) * 32
+        lens = rng.integers(2, 30, size=nr)
+        v = np.unique(np.concatenate([np.arange(s, min(65536, s + l)) for s, l in zip(starts, lens)]))
+    return (base | np.sort(v).astype(np.uint32)).astype(np.uint32)
+
+
+def build_pair(rb, orc, a, b):
+    return (rb.Bitmap.from_sorted(a), rb.Bitmap.from_sorted(b), orc.Bitmap.from_sorted(a),
+            orc.Bitmap.from_sorted(b))
+
+
+def test_fig1_on_gpu(rb, orc):
+    arr = np.arange(1000, dtype=np.uint32) * 62
+    runs = np.concatenate([np.arange(2**16, 2**16 + 100), np.arange(2**16 + 101, 2**16 + 201),
+                           np.arange(2**16 + 300, 2**16 + 400)]).astype(np.uint32)
+    evens = np.arange(2 * 2**16, 3 * 2**16, 2, dtype=np.uint32)
+    v = np.concatenate([arr, runs, evens])
+    g = rb.Bitmap.from_sorted(v)
+    lay = g.layout()
+    assert lay["keys"].tolist() == [0, 1, 2] and lay["types"].tolist() == [0, 2, 1]
+    assert lay["cards"].tolist() == [1000, 300, 32768]
+    assert_layout_eq(lay, orc.Bitmap.from_sorted(v).layout(), "fig1")
+    assert np.array_equal(g.to_numpy(), v)
+    assert np.array_equal(g.to_tensor().cpu().numpy().view(np.uint32), v)
+
+
+@pytest.mark.parametrize("ka", ["array", "bitset", "run"])
+@pytest.mark.parametrize("kb", ["array", "bitset", "run"])
+@pytest.mark.parametrize("size", ["small", "large"])
+def test_container_pair_classes(rb, orc, ka, kb, size):
+    """Every type pair x op, on one shared key plus unmatched keys on each side."""
+    rng = np.random.default_rng(hash((ka, kb, size)) % 2**32)
+    a = np.concatenate([chunk(rng, 1, ka, size), chunk(rng, 7, ka, size), chunk(rng, 9, "array", "small")])
+    b = np.concatenate([chunk(rng, 3, kb, size), chunk(rng, 7, kb, size), chunk(rng, 12, "run", "small")])
+    A, B, OA, OB = build_pair(rb, orc, a, b)
+    assert_layout_eq(A.layout(), OA.layout(), "build A")
+    for op in OPS:
+        got = A.op(op, B).layout()
+        assert_layout_eq(got, OA.op(op, OB).layout(), f"{ka}x{kb} {size} op{op}")
+        check_canonical(got)
+        assert A.op_card(op, B) == OA.op_card(op, OB)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_sets(rb, orc, seed):
+    from test_oracle import random_set
+    r = np.random.default_rng(500 + seed)
+    a, b = random_set(r, 5), random_set(r, 5)
+    A, B, OA, OB = build_pair(rb, orc, a, b)
+    assert_layout_eq(A.layout(), OA.layout(), "build")
+    assert np.array_equal(A.to_numpy(), a)
+    for op in OPS:
+        R = A.op(op, B)
+        assert np.array_equal(R.to_numpy(), NP_OPS[op](a, b).astype(np.uint32))
+        assert_layout_eq(R.layout(), OA.op(op, OB).layout(), f"op{op}")
+    j, i, u = A.jaccard(B)
+    assert (j, i, u) == OA.jaccard(OB)
+
+
+def test_plain_workload(rb, orc, workloads_mod):
+    pool = workloads_mod.plain_pair(1)
+    a, b = pool.values(0), pool.values(1)
+    A, B, OA, OB = build_pair(rb, orc, a, b)
+    assert_layout_eq(A.layout(), OA.layout(), "A")
+    assert_layout_eq(B.layout(), OB.layout(), "B")
+    for op in OPS:
+        assert_layout_eq(A.op(op, B).layout(), OA.op(op, OB).layout(), f"op{op}")
+        assert A.op_card(op, B) == OA.op_card(op, OB)
+    assert A.jaccard(B) == OA.jaccard(OB)
+
+
+def test_edges(rb, orc):
+    e = rb.Bitmap.from_sorted(np.zeros(0, np.uint32))
+    assert e.card == 0 and e.n_containers == 0 and e.to_numpy().size == 0
+    top_v = np.array([0, 65535, 65536, 0xFFFF0000, 0xFFFFFFFF], np.uint32)
+    full = np.arange(5 * 65536, 6 * 65536, dtype=np.uint32)            # <0,65535> run
+    t4096 = np.arange(0, 8192, 2, dtype=np.uint32) + 7 * 65536          # 4096 -> array
+    t4097 = np.arange(0, 8194, 2, dtype=np.uint32) + 8 * 65536          # 4097 -> bitset
+    v = np.concatenate([top_v[:3], full, t4096, t4097, top_v[3:]])
+    T = rb.Bitmap.from_sorted(v)
+    OT = orc.Bitmap.from_sorted(v)
+    assert_layout_eq(T.layout(), OT.layout(), "edges")
+    assert T.layout()["types"].tolist() == [0, 0, 2, 0, 1, 0]
+    OE = orc.Bitmap.from_sorted(np.zeros(0, np.uint32))
+    for op in OPS:
+        assert_layout_eq(T.op(op, e).layout(), OT.op(op, OE).layout(), f"x op empty {op}")
+        assert_layout_eq(e.op(op, T).layout(), OE.op(op, OT).layout(), f"empty op x {op}")
+        assert_layout_eq(T.op(op, T).layout(), OT.op(op, OT).layout(), f"self {op}")
+    assert T.op(3, T).n_containers == 0 and T.op(2, T).card == 0
+    assert e.jaccard(e) == (0.0, 0, 0)
+    with pytest.raises(rb.RoaringError) as ei:
+        rb.Bitmap.from_sorted(np.array([5, 3], np.uint32))
+    assert ei.value.status == rb.EINVAL
+    with pytest.raises(rb.RoaringError):
+        rb.Bitmap.from_sorted(np.array([5, 5], np.uint32))
+
+
+def test_schedules_agree(rb, orc):
+    """Lane-sized and warp-sized processing give identical results."""
+    from test_oracle import random_set
+    r = np.random.default_rng(77)
+    a, b = random_set(r, 6), random_set(r, 6)
+    A, B, OA, OB = build_pair(rb, orc, a, b)
+    saved = rb.get_schedule()
+    try:
+        for w, c, s in [(2, 6, 0), (4, 3, 32), (8, 1, 2047)]:
+            rb.set_schedule(w, c, s)
+            for op in OPS:
+                assert_layout_eq(A.op(op, B).layout(), OA.op(op, OB).layout(), f"sched {w},{c},{s} op{op}")
+    finally:
+        rb.set_schedule(saved["warps_per_cta"], saved["ctas_per_sm"], saved["small_intervals"])
+
+
+def _pool(workloads_mod, name, n, hi, seed=None):
+    spec = workloads_mod.scaled(workloads_mod.SPECS[name], n_bitmaps=n, log10_hi=hi, seed=seed)
+    return workloads_mod.make_pool(spec)
+
+
+@pytest.mark.parametrize("name,n,hi", [("sparse", 24, 5.0), ("runs", 16, 5.3), ("batched", 48, 5.2)])
+def test_batch_matches_oracle_and_per_pair(rb, orc, workloads_mod, name, n, hi):
+    pool = _pool(workloads_mod, name, n, hi)
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    O = [orc.Bitmap.from_sorted(v) for v in vals]
+    for i in range(0, pool.n, 5):
+        assert_layout_eq(G[i].layout(), O[i].layout(), f"build {i}")
+    ops, a, b = workloads_mod.pairs(9, 160, pool.n)
+    flags = np.zeros(len(ops), np.uint32)
+    flags[::4] = rb.Q_COUNT_ONLY
+    outs, counts = rb.batch_op(G, ops, a, b, flags)
+    for i in range(len(ops)):
+        exp = O[a[i]].op(int(ops[i]), O[b[i]])
+        assert counts[i] == exp.card, i
+        if flags[i]:
+            assert outs[i] is None
+            continue
+        got = outs[i].layout()
+        assert_layout_eq(got, exp.layout(), f"{name} pair {i} op {ops[i]}")
+        if i % 10 == 0:
+            per = G[a[i]].op(int(ops[i]), G[b[i]]).layout()
+            assert_layout_eq(per, got, f"per-pair {i}")
+    j, ii, uu = rb.batch_jaccard(G, a, b)
+    for i in range(0, len(a), 7):
+        oj, oi, ou = O[a[i]].jaccard(O[b[i]])
+        assert (ii[i], uu[i]) == (oi, ou) and j[i] == oj
+
+
+def test_plan_graph_replay(rb, orc, workloads_mod):
+    pool = _pool(workloads_mod, "batched", 32, 5.0, seed=44)
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    O = [orc.Bitmap.from_sorted(v) for v in vals]
+    ops, a, b = workloads_mod.pairs(3, 200, pool.n)
+    plan = rb.Plan(G, ops, a, b)
+    first, c1 = plan.run()
+    second, c2 = plan.run()           # CUDA graph replay
+    third, c3 = plan.run()
+    assert np.array_equal(c1, c2) and np.array_equal(c1, c3)
+    for i in range(0, len(ops), 3):
+        exp = O[a[i]].op(int(ops[i]), O[b[i]]).layout()
+        assert_layout_eq(first[i].layout(), exp, f"run1 {i}")
+        assert_layout_eq(third[i].layout(), exp, f"run3 {i}")
+    st = plan.stats()
+    assert st["alg_bytes"] > 0 and st["kernel_ms"] > 0
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_multi_way(rb, orc, workloads_mod, op):
+    pool = _pool(workloads_mod, "sparse", 12, 5.0, seed=12)
+    vals = [pool.values(i) for i in range(pool.n)]
+    if op == 0:   # make the intersection non-trivial
+        common = np.arange(0, 2**24, 97, dtype=np.uint32)
+        vals = [np.union1d(v, common).astype(np.uint32) for v in vals]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    O = [orc.Bitmap.from_sorted(v) for v in vals]
+    for k in (1, 2, 5, 12):
+        m, card = rb.multi_op(op, G[:k])
+        exp = orc.Bitmap.multi(op, O[:k])
+        assert card == exp.card
+        assert_layout_eq(m.layout(), exp.layout(), f"multi op{op} k{k}")
+        _, c2 = rb.multi_op(op, G[:k], count_only=True)
+        assert c2 == exp.card
+    m, card = rb.multi_op(op, [])
+    assert card == 0
+
+
+def test_multi_way_mixed_types(rb, orc, workloads_mod):
+    pool = _pool(workloads_mod, "batched", 16, 5.5, seed=21)
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    O = [orc.Bitmap.from_sorted(v) for v in vals]
+    for op in (0, 1):
+        m, card = rb.multi_op(op, G)
+        assert_layout_eq(m.layout(), orc.Bitmap.multi(op, O).layout(), f"mixed op{op}")
