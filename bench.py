@@ -33,7 +33,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_PAIRS = 65536
-DOMINANT = "k_pairs (materialising batch)"
 
 
 def log(*a):
@@ -100,11 +99,15 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(seed_offset=0):
+def make_workload(seed_offset=0, args=None):
     import workloads as W
     t0 = time.time()
-    pool = W.make_pool(W.SPECS["batched"])
-    ops, a, b = W.pairs(4 + seed_offset, N_PAIRS, pool.n)
+    spec = W.SPECS["batched"]
+    if args is not None and (args.pool or args.log10_hi):
+        spec = W.scaled(spec, n_bitmaps=args.pool or None, log10_hi=args.log10_hi or None)
+    pool = W.make_pool(spec)
+    n_pairs = args.pairs if args is not None and args.pairs else N_PAIRS
+    ops, a, b = W.pairs(4 + seed_offset, n_pairs, pool.n)
     log(f"generated pool of {pool.n} bitmaps ({int(pool.sizes().sum()):,} values) in {time.time() - t0:.1f}s")
     return pool, ops, a, b
 
@@ -164,7 +167,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    pool, ops, a, b = make_workload()
+    pool, ops, a, b = make_workload(args=args)
     steps = []
     res = None
     for s in range(args.warmup + args.steps):
@@ -197,7 +200,10 @@ def run_ours(args):
     rb.build()
     rb.lib()
 
-    pool, ops, a, b = make_workload(seed_offset=rank)
+    pool, ops, a, b = make_workload(seed_offset=rank, args=args)
+    n_pairs = len(ops)
+    if args.schedule:
+        rb.set_schedule(*[int(x) for x in args.schedule.split(",")])
     sizes = pool.sizes().astype(np.float64)
     units = float((sizes[a] + sizes[b]).sum())      # input values per step (pairs counted once)
 
@@ -210,8 +216,8 @@ def run_ours(args):
     log(f"rank {rank}: built {len(G)} device bitmaps ({pool_bytes / 1e9:.2f} GB) in {time.time() - t0:.1f}s")
 
     plan_m = rb.Plan(G, ops, a, b)
-    jflags = np.full(N_PAIRS, rb.Q_COUNT_ONLY, np.uint32)
-    plan_j = rb.Plan(G, np.zeros(N_PAIRS, np.uint32), a, b, jflags)
+    jflags = np.full(n_pairs, rb.Q_COUNT_ONLY, np.uint32)
+    plan_j = rb.Plan(G, np.zeros(n_pairs, np.uint32), a, b, jflags)
 
     if args.autotune:
         best, ms = plan_m.autotune(reps=1)
@@ -244,7 +250,7 @@ def run_ours(args):
         outs, counts, inter = step()
         s1.record(stream)
         st = plan_m.stats()
-        kms.append(st["kernel_ms"])
+        kms.append(st)
         alg.append(st["alg_bytes"])
         outb.append(st["out_bytes"])
         for o in outs:
@@ -276,8 +282,8 @@ def run_ours(args):
                 o.free()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t1) / e2e_steps
-    h2d = 2 * (32 * len(G) + 32 * N_PAIRS + 8 * (N_PAIRS + 1) + 128) + 2 * 16 * N_PAIRS
-    d2h = 2 * (40 * N_PAIRS + 128) + 8 * N_PAIRS * 4
+    h2d = 2 * (32 * len(G) + 32 * n_pairs + 8 * (n_pairs + 1) + 128) + 2 * 16 * n_pairs
+    d2h = 2 * (40 * n_pairs + 128) + 8 * n_pairs * 4
     e2e = {"value": units / e2e_s / 1e9, "unit": "Gints/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "what": "rb_batch_op + rb_batch_jaccard from host query arrays, counts/Jaccard to host; "
                    "index resident on the device"}
@@ -288,12 +294,22 @@ def run_ours(args):
         return 0
 
     peak, peak_kind = measured_peaks()
-    kernel_ms = statistics.mean(kms)
-    alg_bytes = statistics.mean(alg)
+    lean_ms = statistics.mean(s["lean_ms"] for s in kms)
+    heavy_ms = statistics.mean(s["heavy_ms"] for s in kms)
+    lean_b = statistics.mean(s["lean_bytes"] for s in kms)
+    heavy_b = statistics.mean(s["heavy_bytes"] for s in kms)
+    if lean_ms >= heavy_ms:
+        dom, kernel_ms, alg_bytes = "k_lean (materialising batch)", lean_ms, lean_b
+    else:
+        dom, kernel_ms, alg_bytes = "k_heavy (materialising batch)", heavy_ms, heavy_b
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    stage_gbs = (lean_b + heavy_b) / ((lean_ms + heavy_ms) / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": args.traffic, "kernel": DOMINANT, "kernel_ms": kernel_ms,
-                "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind}
+                "traffic": args.traffic, "kernel": dom, "kernel_ms": kernel_ms,
+                "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
+                "pair_stage": {"lean_ms": lean_ms, "heavy_ms": heavy_ms, "lean_bytes": lean_b,
+                               "heavy_bytes": heavy_b, "achieved_gbs": stage_gbs, "frac": stage_gbs / peak,
+                               "deferred_pairs": statistics.mean(s["deferred"] for s in kms)}}
 
     # per-pair baseline on the same GPU: rb_apply one pair at a time
     per = per_pair_leg(rb, G, ops, a, b, sizes, n=args.per_pair_sample)
@@ -304,12 +320,13 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u16/u64 integer", "data": "synthetic (seeded)",
             "config": {"workload": "batched: 4096-bitmap pool over [0,2^32), c log-uniform 10..1e7, 40/30/30 "
                                    "sparse/dense/runs; 65,536 pairs AND/OR/ANDNOT/XOR 40/30/15/15 materialised "
-                                   "+ Jaccard count batch", "global_batch": N_PAIRS * ws,
+                                   "+ Jaccard count batch", "global_batch": n_pairs * ws,
                        "pool_bytes": pool_bytes, "units_per_step": units,
                        "l2": "inputs larger than L2 (pool and outputs are GBs), no flush",
                        "parallelism": f"replicas x{ws}", "schedule": rb.get_schedule()},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 3 * args.steps,
+            # per step: k_lean + k_heavy + k_compact (materialising batch), k_lean + k_heavy (Jaccard batch)
+            "gpu_launches": 5 * args.steps,
             "clocks": clk,
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
             "per_pair": per}
@@ -353,6 +370,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=10.0)
     ap.add_argument("--per-pair-sample", type=int, default=512)
+    ap.add_argument("--pool", type=int, default=0, help="scaled case: number of pool bitmaps (profiling)")
+    ap.add_argument("--pairs", type=int, default=0, help="scaled case: number of pairs (profiling)")
+    ap.add_argument("--log10-hi", type=float, default=0.0, help="scaled case: top of the cardinality law")
+    ap.add_argument("--schedule", default="", help="warps_per_cta,ctas_per_sm,small_intervals")
     ap.add_argument("--traffic", type=float, default=None,
                     help="dram bytes per launch of the dominant kernel from an ncu capture")
     args = ap.parse_args()

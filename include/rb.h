@@ -159,23 +159,32 @@ typedef struct rb_plan rb_plan_t;
 rb_status rb_plan_create(const rb_t *const *pool, uint32_t pool_n, const rb_query *q, uint64_t nq,
                          void *stream, rb_plan_t **out);
 rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream);
-/* Time of the last run's container-pair kernel (device milliseconds), the
- * algorithmic bytes it moved, and the bytes of the arena it wrote. */
-rb_status rb_plan_stats(const rb_plan_t *p, double *kernel_ms, uint64_t *alg_bytes,
-                        uint64_t *out_bytes);
+/* Measurements of the last run, from CUDA events on the stream the kernels
+ * ran on: the container-pair stage is a lean kernel (key merge, small pairs)
+ * then a heavy kernel (pairs deferred by the lean one: bitsets, many values
+ * or runs).  *_bytes are the algorithmic bytes each kernel moved (input and
+ * output payloads, 10 bytes of key + descriptor per container), counted by
+ * the kernels themselves; deferred is the number of deferred pairs. */
+typedef struct {
+    double lean_ms, heavy_ms;
+    uint64_t lean_bytes, heavy_bytes, alg_bytes, out_bytes, deferred;
+} rb_plan_timing;
+rb_status rb_plan_stats(const rb_plan_t *p, rb_plan_timing *t);
 void rb_plan_free(rb_plan_t *p);
 
 /* ------------------------------------------------------------ schedules */
 
-/* Launch schedule of the container-pair kernels: warps per CTA (2, 4 or 8),
- * CTAs per SM, and the largest container pair, in intervals (array values or
- * runs on both sides), that one lane processes alone; bigger pairs are
- * processed by a whole warp. */
+/* Launch schedule of the container-pair kernels: the heavy kernel's warps
+ * per CTA (2, 4 or 8; each warp owns 16 KB of shared tiles) and CTAs per SM;
+ * the largest container pair, in intervals (array values or runs on both
+ * sides), that one lane of the lean kernel sweeps alone (bigger pairs and all
+ * bitsets are deferred to the heavy kernel); and the lean kernel's CTAs of
+ * 256 threads per SM (0 = 4). */
 typedef struct {
     uint32_t warps_per_cta;
     uint32_t ctas_per_sm;
     uint32_t small_intervals;
-    uint32_t reserved;
+    uint32_t lean_ctas_per_sm;
 } rb_schedule;
 rb_status rb_set_schedule(const rb_schedule *s);
 rb_status rb_get_schedule(rb_schedule *s);

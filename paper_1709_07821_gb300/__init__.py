@@ -37,11 +37,17 @@ class Query(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("small_intervals", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("small_intervals", ctypes.c_uint32), ("lean_ctas_per_sm", ctypes.c_uint32)]
 
     def as_dict(self):
         return {"warps_per_cta": self.warps_per_cta, "ctas_per_sm": self.ctas_per_sm,
-                "small_intervals": self.small_intervals}
+                "small_intervals": self.small_intervals, "lean_ctas_per_sm": self.lean_ctas_per_sm}
+
+
+class PlanTiming(ctypes.Structure):
+    _fields_ = [("lean_ms", ctypes.c_double), ("heavy_ms", ctypes.c_double), ("lean_bytes", ctypes.c_uint64),
+                ("heavy_bytes", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64), ("out_bytes", ctypes.c_uint64),
+                ("deferred", ctypes.c_uint64)]
 
 
 class Request(ctypes.Structure):
@@ -81,7 +87,7 @@ def _sig(L):
         "rb_batch_jaccard": [vp, u32, vp, vp, u64, vp, vp, vp, vp],
         "rb_plan_create": [vp, u32, vp, u64, vp, pvp],
         "rb_plan_run": [vp, vp, vp, vp],
-        "rb_plan_stats": [vp, pdbl, pu64, pu64],
+        "rb_plan_stats": [vp, ctypes.POINTER(PlanTiming)],
         "rb_set_schedule": [ctypes.POINTER(Schedule)],
         "rb_get_schedule": [ctypes.POINTER(Schedule)],
         "rb_autotune": [vp, u32, vp, ctypes.POINTER(Schedule), pdbl],
@@ -344,9 +350,11 @@ class Plan:
         return bms, counts
 
     def stats(self):
-        ms, alg, ob = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
-        _check(lib().rb_plan_stats(self._h, ctypes.byref(ms), ctypes.byref(alg), ctypes.byref(ob)))
-        return {"kernel_ms": ms.value, "alg_bytes": alg.value, "out_bytes": ob.value}
+        t = PlanTiming()
+        _check(lib().rb_plan_stats(self._h, ctypes.byref(t)))
+        return {"lean_ms": t.lean_ms, "heavy_ms": t.heavy_ms, "kernel_ms": t.lean_ms + t.heavy_ms,
+                "lean_bytes": t.lean_bytes, "heavy_bytes": t.heavy_bytes, "alg_bytes": t.alg_bytes,
+                "out_bytes": t.out_bytes, "deferred": t.deferred}
 
     def autotune(self, reps=2, stream=None):
         s = Schedule()
@@ -372,8 +380,8 @@ def get_schedule() -> dict:
     return s.as_dict()
 
 
-def set_schedule(warps_per_cta: int, ctas_per_sm: int, small_intervals: int):
-    s = Schedule(warps_per_cta, ctas_per_sm, small_intervals, 0)
+def set_schedule(warps_per_cta: int, ctas_per_sm: int, small_intervals: int, lean_ctas_per_sm: int = 0):
+    s = Schedule(warps_per_cta, ctas_per_sm, small_intervals, lean_ctas_per_sm)
     _check(lib().rb_set_schedule(ctypes.byref(s)))
 
 

@@ -19,7 +19,7 @@ std::mutex g_alloc_mu;
 rb_alloc_fn g_alloc = nullptr;
 rb_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
-rb_schedule g_sched = {4, 3, 32, 0};
+rb_schedule g_sched = {4, 3, 64, 0};
 std::mutex g_sched_mu;
 }  // namespace
 
@@ -460,6 +460,7 @@ rb_status rb_set_schedule(const rb_schedule *s) {
     if (s->ctas_per_sm < 1 || s->ctas_per_sm * s->warps_per_cta * 16384u > 228u * 1024u)
         return set_err(RB_EINVAL, "ctas_per_sm out of range for 16 KB of tiles per warp");
     if (s->small_intervals > 2047) return set_err(RB_EINVAL, "small_intervals must be <= 2047");
+    if (s->lean_ctas_per_sm > 8) return set_err(RB_EINVAL, "lean_ctas_per_sm must be <= 8");
     std::lock_guard<std::mutex> g(g_sched_mu);
     g_sched = *s;
     return RB_OK;

@@ -1,23 +1,28 @@
 // rb_pairs.cu - pairwise operations: key merge, container-pair kernels,
 // canonical compaction, batches, plans (CUDA graphs) and the autotuner.
 //
-// Work decomposition.  Every query (a op b) owns a range of "slots"; a slot
-// is one key of one input and becomes at most one output container:
-//   AND (and every count-only query): the keys of the input with fewer keys;
-//   ANDNOT: the keys of a;  OR / XOR: the keys of a, then the keys of b.
-// A slot finds its partner by binary search in the other key array (the key
-// merge of Sec. 5's profiles, done per slot), so a key present in both
-// inputs becomes one container pair.  Its output position keeps the key
-// order of the result: the slot index for AND/ANDNOT, and for OR/XOR the
-// merge-path position in the multiset of both key lists (a's key first on a
-// tie; b's copy of a shared key only marks its position empty).  Every
-// position of a query's slot range is written exactly once, so the
-// compaction pass only has to drop empty results.
-// Slots are cut into tiles of 32; warps of a persistent kernel steal tiles
-// from one atomic counter.  In a tile each lane resolves its container pair;
-// small pairs (few values or runs on both sides) are merged by the lane alone
-// with an interval sweep, large ones by the whole warp through 8 KB shared
-// tiles (bitset operands are read straight from global memory).
+// Work decomposition.  Every query (a op b) owns a range of "slots", cut into
+// tiles of 32 that the warps of a persistent kernel steal from one atomic
+// counter.  Two slot modes:
+//   merge  - slot d is element d of the merge of both key lists (a's key first
+//            on a tie).  A tile finds where its 32 elements start with a
+//            cooperative 32-ary merge-path search and reads both key windows
+//            with one coalesced load each.  Used for OR/XOR always and for
+//            AND/ANDNOT/counts when the key counts are within a factor of 8.
+//   driver - slot i is key i of one input (the smaller one for AND and
+//            counts, a for ANDNOT), and each lane binary-searches the other
+//            key list.  Used for skewed AND/ANDNOT/count queries.
+// A key present in both inputs becomes one container pair (Sec. 1: containers
+// are matched by their 16-bit key).  Output positions keep the result's key
+// order: the merged index for OR/XOR (b's copy of a shared key only marks its
+// position empty), a's key index for AND/ANDNOT.  Every position of a query's
+// output range is written exactly once, so compaction only drops empties.
+//
+// Kernels.  k_lean (high occupancy, no shared tiles) does the key merge of a
+// tile and finishes every small container pair with a one-lane interval sweep;
+// pairs with a bitset or many values/runs go to a deferred queue that k_heavy
+// (one warp per pair, two 8 KB shared tiles per warp) drains.  k_compact then
+// drops the empty results of every query.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -30,28 +35,39 @@ using namespace rbd;
 
 namespace {
 
-constexpr uint32_t F_COUNT = 1;
+constexpr uint32_t F_COUNT = 1, F_MERGE = 2;
 enum : uint32_t { K_NONE = 0, K_EMPTY = 1, K_PAIR = 2, K_COPY_A = 3, K_COPY_B = 4 };
+constexpr int LEAN_THREADS = 128;
+constexpr uint32_t KEY_END = 0x10000u;   // past-the-end key sentinel
 
 struct PairDev {
     uint32_t a, b, op, flags;
-    uint32_t n_slots, pad;
-    unsigned long long slot_base;
+    uint32_t n_slots, n_pos;
+    unsigned long long pos_base;
 };
 
 struct PairStats {
     unsigned long long card;      // output cardinality (count-only: |a n b|)
     unsigned long long words;     // word-region bytes of the output
     unsigned long long in_bytes;  // algorithmic input bytes read
-    unsigned int n_out, m, nbits, pad;
+    unsigned int n_out, pad0, nbits, pad1;
+};
+
+struct Deferred {
+    unsigned long long da, db;
+    uint32_t p, pos;
+    uint32_t kind_key, pad;
 };
 
 struct ExecState {
     uint8_t *arena;
     uint16_t *keys;
     uint64_t *descs;
+    Deferred *defer;
     unsigned long long words_off, words_cap, bits_off, bits_cap;
-    unsigned long long words_used, bits_used, work;
+    unsigned long long words_used, bits_used, work, hwork;
+    unsigned long long defer_cap, defer_n;
+    unsigned long long lean_bytes, heavy_bytes;
     unsigned int status, pad;
 };
 
@@ -204,13 +220,110 @@ __device__ uint32_t warp_count_and(const CRef &a, const CRef &b, uint64_t *T0, u
     return c;
 }
 
-// ------------------------------------------------------------ one tile
+// ------------------------------------------------------------ key merge
 
-__device__ void pair_tile(const PairParams &P, unsigned long long t, uint64_t *T0, uint64_t *T1, uint32_t lane) {
-    // the query owning tile t: largest p with tile_base[p] <= t
+// number of a's keys among the first d elements of the merge of a and b
+// (a first on a tie), by a cooperative 32-ary search: each round the warp
+// evaluates "a[i] precedes b[d-1-i]" at 32 evenly spaced i and keeps the
+// stretch where it turns false (4 rounds for 65536 keys)
+__device__ __forceinline__ uint32_t merge_split(const uint16_t *ka, uint32_t na, const uint16_t *kb, uint32_t nb,
+                                                uint32_t d, uint32_t lane) {
+    uint32_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (hi > lo) {
+        const uint32_t span = hi - lo;
+        if (span <= 32) {
+            bool pr = false;
+            if (lane < span) {
+                const uint32_t i = lo + lane;
+                pr = __ldg(ka + i) <= __ldg(kb + (d - 1 - i));
+            }
+            lo += __popc(__ballot_sync(FULL, pr));
+            break;
+        }
+        const uint32_t step = (span + 31) / 32;
+        const uint32_t i = lo + lane * step;
+        bool pr = false;
+        if (i < hi) pr = __ldg(ka + i) <= __ldg(kb + (d - 1 - i));
+        const uint32_t k = __popc(__ballot_sync(FULL, pr));
+        if (k == 0) break;   // a[lo] does not precede: the split is lo
+        const uint32_t nlo = lo + (k - 1) * step + 1;
+        hi = min(hi, lo + k * step);
+        lo = nlo;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------ array merges
+
+// Sec. 1 membership rule as a 4-bit table indexed by (element comes from a) * 2
+// + (the other input has it): AND keeps a's shared values, OR keeps all of a
+// and b's unshared ones, ANDNOT a's unshared ones, XOR every unshared value
+__device__ __forceinline__ uint32_t keep_table(uint32_t op) {
+    return op == OP_AND ? 0x8u : op == OP_OR ? 0xDu : op == OP_ANDNOT ? 0x4u : 0x5u;
+}
+
+// one lane merges two small sorted arrays without branches on the data: each
+// step takes the smaller head (a first on a tie), notes whether the other
+// input holds it, and keeps it by the op's table; counts cardinality c and
+// runs r, and with EMIT writes the kept values
+template <bool EMIT>
+__device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *a, uint32_t na, const uint16_t *b,
+                                                  uint32_t nb, uint32_t &c, uint32_t &r, uint16_t *out) {
+    uint32_t i = 0, j = 0, pa = 0xFFFFFFFFu, last = 0xFFFFFFFEu;
+    c = 0;
+    r = 0;
+    const bool keep_b = (tbl & 1u) != 0;   // AND/ANDNOT stop once a is exhausted
+    while (i < na || (keep_b && j < nb)) {
+        const uint32_t va = i < na ? (uint32_t)__ldg(a + i) : KEY_END;
+        const uint32_t vb = j < nb ? (uint32_t)__ldg(b + j) : KEY_END;
+        const bool ta = va <= vb;
+        const uint32_t v = ta ? va : vb;
+        const bool ino = ta ? (vb == va) : (pa == vb);
+        if ((tbl >> ((ta ? 2u : 0u) | (ino ? 1u : 0u))) & 1u) {
+            if (EMIT) out[c] = (uint16_t)v;
+            r += (v != last + 1);
+            last = v;
+            c++;
+        }
+        pa = ta ? va : pa;
+        i += ta;
+        j += !ta;
+    }
+}
+
+// ------------------------------------------------------------ lean kernel
+
+enum : uint32_t { M_NONE = 0, M_LANE_ARR, M_LANE_SWEEP, M_LANE_COPY, M_WARP_ARR, M_WARP_COPY, M_DEFER };
+constexpr uint32_t WARP_MERGE_MAX = 1024;   // values of both arrays the warp merges through shared memory
+constexpr uint32_t RUN_SWEEP_MAX = 512;     // intervals one lane sweeps when runs are involved
+constexpr uint32_t LANE_COPY_MAX = 256;     // 4-byte words one lane copies
+constexpr uint32_t QCAP = 64;               // container pairs queued per warp
+
+// a container pair waiting in a warp's queue
+struct Item {
+    unsigned long long da, db;
+    uint32_t p, pos;
+    uint32_t info;   // key | kind << 16 | mode << 20
+    uint32_t pad;
+};
+
+// bytes reserved for an array-by-array result before it is computed: the
+// array encoding of the largest possible result (the run encoding, chosen
+// only when smaller, also fits)
+__device__ __forceinline__ uint32_t array_result_bound(uint32_t op, uint32_t na, uint32_t nb) {
+    const uint32_t n = op == OP_AND ? min(na, nb) : op == OP_ANDNOT ? na : na + nb;
+    return (2 * n + 3) & ~3u;
+}
+
+// Key merge of one tile: each lane resolves its slot into a container pair,
+// an empty result or nothing.  Empty results are written at once, pairs with
+// a bitset or many values go to the heavy kernel's queue, and the others are
+// appended to the warp's item queue q (qn stays warp-uniform).
+__device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t *win, Item *q, uint32_t &qn,
+                             unsigned long long &meta, uint32_t lane) {
     uint32_t lo = 0, hi = P.n_pairs;
     while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
+        const uint32_t mid = (lo + hi) >> 1;
         if (P.tile_base[mid] <= t) lo = mid;
         else hi = mid;
     }
@@ -220,123 +333,254 @@ __device__ void pair_tile(const PairParams &P, unsigned long long t, uint64_t *T
     ExecState *es = P.es;
     const uint32_t op = pd.op;
     const bool count_only = (pd.flags & F_COUNT) != 0;
-    const uint32_t slot = (uint32_t)(t - P.tile_base[p]) * 32u + lane;
+    const uint32_t local = (uint32_t)(t - P.tile_base[p]);
 
-    // ---- key merge for this lane's slot
-    uint32_t kind = K_NONE, key = 0, pos = 0, ia = 0, ib = 0, matchedA = 0;
-    if (slot < pd.n_slots) {
-        if (count_only || op == OP_AND) {
-            const bool drvA = A.n <= B.n;
-            const uint16_t *dk = drvA ? A.keys : B.keys;
-            const uint16_t *ok = drvA ? B.keys : A.keys;
-            const uint32_t on = drvA ? B.n : A.n;
-            key = __ldg(dk + slot);
-            const uint32_t j = lower_bound16(ok, on, key);
-            pos = slot;
-            if (j < on && __ldg(ok + j) == key) {
-                kind = K_PAIR;
-                ia = drvA ? slot : j;
-                ib = drvA ? j : slot;
-            } else {
-                kind = K_EMPTY;
+    uint32_t kind = K_NONE, key = 0, pos = 0, ia = 0, ib = 0;
+    if (pd.flags & F_MERGE) {
+        const uint32_t d0 = local * 32u;
+        const uint32_t i0 = merge_split(A.keys, A.n, B.keys, B.n, d0, lane);
+        const uint32_t j0 = d0 - i0;
+        uint32_t *WA = win;        // WA[0] = a[i0-1], WA[1..32] = a[i0..i0+31]
+        uint32_t *WB = win + 33;   // WB[0..31] = b[j0..j0+31]
+        WA[1 + lane] = i0 + lane < A.n ? (uint32_t)__ldg(A.keys + i0 + lane) : KEY_END;
+        WB[lane] = j0 + lane < B.n ? (uint32_t)__ldg(B.keys + j0 + lane) : KEY_END;
+        if (lane == 0) WA[0] = i0 > 0 ? (uint32_t)__ldg(A.keys + i0 - 1) : 0xFFFFFFFFu;
+        __syncwarp();
+        if (d0 + lane < A.n + B.n) {
+            // x = a's keys among this tile's first `lane` elements
+            uint32_t xl = 0, xh = lane;
+            while (xl < xh) {
+                const uint32_t m = (xl + xh) >> 1;
+                if (WA[1 + m] <= WB[lane - 1 - m]) xl = m + 1;
+                else xh = m;
             }
-        } else if (op == OP_ANDNOT) {
-            key = __ldg(A.keys + slot);
-            const uint32_t j = lower_bound16(B.keys, B.n, key);
-            pos = slot;
-            ia = slot;
-            if (j < B.n && __ldg(B.keys + j) == key) { kind = K_PAIR; ib = j; }
-            else kind = K_COPY_A;
-        } else if (slot < A.n) {
-            key = __ldg(A.keys + slot);
-            const uint32_t j = lower_bound16(B.keys, B.n, key);
-            pos = slot + j;
-            ia = slot;
-            if (j < B.n && __ldg(B.keys + j) == key) { kind = K_PAIR; ib = j; matchedA = 1; }
-            else kind = K_COPY_A;
-        } else {
-            // merge-path position over the multiset of both key lists (a's
-            // key first on a tie): a key b shares with a sits right after a's
-            // and only marks its position empty
-            const uint32_t jb = slot - A.n;
-            key = __ldg(B.keys + jb);
-            const uint32_t i = lower_bound16(A.keys, A.n, key);
-            if (i < A.n && __ldg(A.keys + i) == key) { kind = K_EMPTY; pos = jb + i + 1; }
-            else { kind = K_COPY_B; ib = jb; pos = jb + i; }
+            const uint32_t av = WA[1 + xl], bv = WB[lane - xl];
+            const uint32_t ai = i0 + xl, bj = j0 + lane - xl;
+            if (av <= bv) {   // a's key ai; b has it too iff bv == av
+                key = av;
+                const bool m = bv == av;
+                pos = (op == OP_OR || op == OP_XOR) ? d0 + lane : ai;
+                ia = ai;
+                ib = bj;
+                if (count_only) kind = m ? K_PAIR : K_NONE;
+                else if (m) kind = K_PAIR;
+                else kind = (op == OP_AND) ? K_EMPTY : K_COPY_A;
+            } else {          // b's key bj; shared iff a's previous key equals it
+                key = bv;
+                const bool m = WA[xl] == bv;
+                if (!count_only && (op == OP_OR || op == OP_XOR)) {
+                    pos = d0 + lane;
+                    ib = bj;
+                    kind = m ? K_EMPTY : K_COPY_B;
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        const uint32_t slot = local * 32u + lane;
+        if (slot < pd.n_slots) {
+            if (count_only || op == OP_AND) {
+                const bool drvA = A.n <= B.n;
+                const uint16_t *dk = drvA ? A.keys : B.keys;
+                const uint16_t *ok = drvA ? B.keys : A.keys;
+                const uint32_t on = drvA ? B.n : A.n;
+                key = __ldg(dk + slot);
+                const uint32_t j = lower_bound16(ok, on, key);
+                pos = slot;
+                if (j < on && __ldg(ok + j) == key) {
+                    kind = K_PAIR;
+                    ia = drvA ? slot : j;
+                    ib = drvA ? j : slot;
+                } else {
+                    kind = count_only ? K_NONE : K_EMPTY;
+                }
+            } else {   // ANDNOT, driven by a
+                key = __ldg(A.keys + slot);
+                const uint32_t j = lower_bound16(B.keys, B.n, key);
+                pos = slot;
+                ia = slot;
+                if (j < B.n && __ldg(B.keys + j) == key) { kind = K_PAIR; ib = j; }
+                else kind = K_COPY_A;
+            }
         }
     }
     const uint64_t da = (kind == K_PAIR || kind == K_COPY_A) ? __ldg(A.descs + ia) : 0ull;
     const uint64_t db = (kind == K_PAIR || kind == K_COPY_B) ? __ldg(B.descs + ib) : 0ull;
-    unsigned long long inb = 0;
-    if (kind == K_PAIR) inb = in_payload_bytes(da) + in_payload_bytes(db) + 18;
-    else if (kind == K_COPY_A) inb = in_payload_bytes(da) + 10;
-    else if (kind == K_COPY_B) inb = in_payload_bytes(db) + 10;
-    else if (kind == K_EMPTY) inb = 10;
+    meta += kind == K_PAIR ? 20 : (kind == K_NONE ? 0 : 10);   // keys and descriptors read
 
-    if (count_only) {
-        // Sec. 5 "Fast counts": only |a n b| is computed
-        uint32_t cnt = 0;
-        bool large = false;
-        if (kind == K_PAIR) {
-            if (n_intervals(da) + n_intervals(db) <= P.small_iv) {
-                uint32_t c, r;
-                const CRef ca = cref(A.base, da), cb = cref(B.base, db);
-                lane_sweep<false>(OP_AND, iv_src(ca), iv_src(cb), c, r, 0, nullptr);
-                cnt = c;
+    // who does the work: one lane (array merges, run sweeps, short copies),
+    // the whole warp (large array pairs, long copies) or the heavy kernel
+    uint32_t mode = M_NONE;
+    if (kind == K_PAIR) {
+        const uint32_t ta = d_type(da), tb = d_type(db);
+        if (ta == T_ARRAY && tb == T_ARRAY) {
+            const uint32_t n = d_card(da) + d_card(db);
+            mode = n <= P.small_iv ? M_LANE_ARR : n <= WARP_MERGE_MAX ? M_WARP_ARR : M_DEFER;
+        } else if (ta != T_BITSET && tb != T_BITSET && n_intervals(da) + n_intervals(db) <= RUN_SWEEP_MAX) {
+            mode = M_LANE_SWEEP;
+        } else {
+            mode = M_DEFER;
+        }
+    } else if (kind == K_COPY_A || kind == K_COPY_B) {
+        const uint64_t dx = kind == K_COPY_A ? da : db;
+        if (d_type(dx) == T_BITSET) mode = M_DEFER;
+        else mode = word_alloc_bytes(d_type(dx), d_card(dx), d_runs(dx)) <= 4 * LANE_COPY_MAX ? M_LANE_COPY
+                                                                                              : M_WARP_COPY;
+    }
+    const uint32_t lm = __ballot_sync(FULL, mode == M_DEFER);
+    if (lm) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&es->defer_n, (unsigned long long)__popc(lm));
+        base = __shfl_sync(FULL, base, 0);
+        if (mode == M_DEFER) {
+            const unsigned long long at = base + __popc(lm & lanemask_lt(lane));
+            if (at < es->defer_cap) {
+                Deferred d;
+                d.da = da;
+                d.db = db;
+                d.p = p;
+                d.pos = pos;
+                d.kind_key = (kind << 16) | key;
+                d.pad = 0;
+                es->defer[at] = d;
             } else {
-                large = true;
+                atomicOr(&es->status, 2u);
             }
         }
-        unsigned long long wc = 0;
-        uint32_t lm = __ballot_sync(FULL, large);
-        while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const uint64_t xa = __shfl_sync(FULL, da, src), xb = __shfl_sync(FULL, db, src);
-            wc += warp_count_and(cref(A.base, xa), cref(B.base, xb), T0, T1, lane);
-        }
-        const unsigned long long tot = warp_sum64(cnt) + wc, ib_tot = warp_sum64(inb);
-        if (lane == 0) {
-            if (tot) atomicAdd(&P.stats[p].card, tot);
-            atomicAdd(&P.stats[p].in_bytes, ib_tot);
-        }
-        return;
     }
+    if (kind == K_EMPTY) {
+        es->descs[pd.pos_base + pos] = DESC_EMPTY;
+        es->keys[pd.pos_base + pos] = (uint16_t)key;
+    }
+    const bool act = mode != M_NONE && mode != M_DEFER;
+    const uint32_t am = __ballot_sync(FULL, act);
+    if (act) {
+        Item it;
+        it.da = da;
+        it.db = db;
+        it.p = p;
+        it.pos = pos;
+        it.info = key | (kind << 16) | (mode << 20);
+        it.pad = 0;
+        q[qn + __popc(am & lanemask_lt(lane))] = it;
+    }
+    qn += __popc(am);
+    __syncwarp();
+}
 
-    // ---- materialise
-    bool small = false, large = false;
-    if (kind == K_PAIR) {
-        if (n_intervals(da) + n_intervals(db) <= P.small_iv) small = true;
-        else large = true;
-    } else if (kind == K_COPY_A || kind == K_COPY_B) {
-        if (n_intervals(kind == K_COPY_A ? da : db) <= P.small_iv) small = true;
-        else large = true;
+// The warp merges two sorted arrays (na + nb <= 1024) through shared memory:
+// coalesced staging, the merged sequence cut into 32 equal chunks found by
+// merge-path binary search, one chunk per lane (recording which input each
+// step took and which values it kept), a warp scan to place the kept values,
+// and the canonical encoding.  off is the reserved output (ALLOC_FAIL: count
+// only).  Returns the descriptor; card gets the cardinality.
+__device__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, const uint16_t *ga, uint32_t na,
+                                      const uint16_t *gb, uint32_t nb, uint16_t *stg, uint32_t lane, uint64_t off,
+                                      uint32_t &card) {
+    uint16_t *SA = stg, *SB = stg + na, *SO = stg + WARP_MERGE_MAX;
+    for (uint32_t x = lane; x < na; x += 32) SA[x] = __ldg(ga + x);
+    for (uint32_t x = lane; x < nb; x += 32) SB[x] = __ldg(gb + x);
+    __syncwarp();
+    const uint32_t tot = na + nb, L = (tot + 31) >> 5;
+    const uint32_t d = min(lane * L, tot), dend = min(d + L, tot);
+    uint32_t lo = d > nb ? d - nb : 0, hi = min(d, na);
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (SA[m] <= SB[d - 1 - m]) lo = m + 1;
+        else hi = m;
     }
-    uint32_t lc = 0, lr = 0, lt = 0, lbytes = 0;
-    CRef ca, cb;
-    ca.p = nullptr;
-    cb.p = nullptr;
-    if (small) {
-        if (kind == K_PAIR) {
-            ca = cref(A.base, da);
-            cb = cref(B.base, db);
+    const uint32_t i0 = lo, j0 = d - lo;
+    uint32_t i = i0, j = j0, pa = i0 > 0 ? (uint32_t)SA[i0 - 1] : 0xFFFFFFFFu;
+    uint32_t take_a = 0, kept = 0, c = 0, r = 0, first = 0, last = 0xFFFFFFFEu;
+    for (uint32_t s = 0; d + s < dend; s++) {
+        const uint32_t va = i < na ? (uint32_t)SA[i] : KEY_END, vb = j < nb ? (uint32_t)SB[j] : KEY_END;
+        const bool ta = va <= vb;
+        const uint32_t v = ta ? va : vb;
+        const bool ino = ta ? (vb == va) : (pa == vb);
+        take_a |= (uint32_t)ta << s;
+        if ((tbl >> ((ta ? 2u : 0u) | (ino ? 1u : 0u))) & 1u) {
+            kept |= 1u << s;
+            if (c == 0) first = v;
+            r += (v != last + 1);
+            last = v;
+            c++;
+        }
+        pa = ta ? va : pa;
+        i += ta;
+        j += !ta;
+    }
+    // a lane's first kept value continues a run when it follows the last kept
+    // value of the lanes before it (values increase, so a max-scan finds it)
+    uint32_t m = c ? last + 1 : 0;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, m, dd);
+        if (lane >= (uint32_t)dd) m = max(m, y);
+    }
+    uint32_t prev = __shfl_up_sync(FULL, m, 1);
+    if (lane == 0) prev = 0;
+    if (c && prev != 0 && first == prev) r--;
+    const uint32_t cincl = warp_incl(c, lane);
+    const uint32_t C = __shfl_sync(FULL, cincl, 31), R = warp_sum(r);
+    card = C;
+    uint64_t desc = DESC_EMPTY;
+    if (off != ALLOC_FAIL && C) {
+        const uint32_t ty = canon_type(C, R);   // C <= 1024: array or runs
+        uint32_t qq = cincl - c;
+        i = i0;
+        j = j0;
+        for (uint32_t s = 0; d + s < dend; s++) {
+            const bool ta = (take_a >> s) & 1u;
+            const uint16_t v = ta ? SA[i] : SB[j];
+            i += ta;
+            j += !ta;
+            if ((kept >> s) & 1u) SO[qq++] = v;
+        }
+        __syncwarp();
+        if (ty == T_ARRAY) l_emit_array(SO, C, reinterpret_cast<uint16_t *>(es->arena + off), lane);
+        else l_emit_runs(SO, C, R, stg, reinterpret_cast<uint32_t *>(es->arena + off), lane);
+        desc = mk_desc(C, ty, ty == T_RUN ? R : 0, off);
+    }
+    __syncwarp();
+    return desc;
+}
+
+// Process n <= 32 queued container pairs, one per lane (warp-sized ones by
+// the whole warp in turn), with one allocation for all their outputs.
+__device__ void process_items(const PairParams &P, const Item *q, uint32_t n, uint16_t *stg,
+                              unsigned long long &bytes_acc, uint32_t lane) {
+    ExecState *es = P.es;
+    const bool has = lane < n;
+    Item it;
+    it.da = it.db = 0;
+    it.p = it.pos = it.info = it.pad = 0;
+    if (has) it = q[lane];
+    const uint32_t mode = has ? (it.info >> 20) & 7u : M_NONE;
+    const uint32_t kind = (it.info >> 16) & 7u, key = it.info & 0xFFFFu;
+    const PairDev pd = P.pairs[it.p];
+    const uint8_t *abase = P.pool[pd.a].base, *bbase = P.pool[pd.b].base;
+    const bool count = (pd.flags & F_COUNT) != 0;
+    const uint32_t op = count ? (uint32_t)OP_AND : pd.op;
+    const uint32_t tbl = keep_table(op);
+    const uint64_t dx = kind == K_COPY_B ? it.db : it.da;
+    const CRef ca = cref(kind == K_COPY_B ? bbase : abase, dx), cb = cref(bbase, it.db);
+
+    // sizes: exact for copies and run sweeps, the array bound for array merges
+    uint32_t bytes = 0, lc = 0, lr = 0, lt = 0;
+    if (!count) {
+        if (mode == M_LANE_ARR || mode == M_WARP_ARR) {
+            bytes = array_result_bound(op, ca.card, cb.card);
+        } else if (mode == M_LANE_SWEEP) {
             lane_sweep<false>(op, iv_src(ca), iv_src(cb), lc, lr, 0, nullptr);
             if (lc) {
                 lt = canon_type(lc, lr);
-                lbytes = word_alloc_bytes(lt, lc, lr);
+                bytes = word_alloc_bytes(lt, lc, lr);
             }
-        } else {
-            const uint64_t dx = kind == K_COPY_A ? da : db;
-            ca = cref(kind == K_COPY_A ? A.base : B.base, dx);
-            lc = ca.card;
-            lr = ca.runs;
-            lt = ca.type;
-            lbytes = word_alloc_bytes(lt, lc, lr);
+        } else if (mode == M_LANE_COPY || mode == M_WARP_COPY) {
+            bytes = word_alloc_bytes(ca.type, ca.card, ca.runs);
         }
     }
-    // one atomic per warp for all lane-sized outputs
-    const uint32_t incl = warp_incl(lbytes, lane);
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
     unsigned long long wbase = 0;
     bool ok = true;
     if (total) {
@@ -345,84 +589,184 @@ __device__ void pair_tile(const PairParams &P, unsigned long long t, uint64_t *T
         ok = wbase + total <= es->words_cap;
         if (!ok && lane == 0) atomicOr(&es->status, 1u);
     }
-    uint16_t *OKEY = es->keys + pd.slot_base;
-    uint64_t *ODESC = es->descs + pd.slot_base;
-    unsigned long long card_acc = 0, words_acc = 0;
-    uint32_t bits_acc = 0;
-    if (small) {
-        uint64_t desc = DESC_EMPTY;
-        if (lc && ok) {
-            const uint64_t off = es->words_off + wbase + incl - lbytes;
-            uint8_t *dst = es->arena + off;
-            if (kind == K_PAIR) {
-                uint32_t c2, r2;
-                lane_sweep<true>(op, iv_src(ca), iv_src(cb), c2, r2, lt, dst);
-            } else {
-                const uint32_t *S = reinterpret_cast<const uint32_t *>(ca.p);
-                uint32_t *D = reinterpret_cast<uint32_t *>(dst);
-                for (uint32_t i = 0; i < lbytes / 4; i++) D[i] = __ldg(S + i);
+    const uint64_t off = (ok && bytes) ? es->words_off + wbase + incl - bytes : ALLOC_FAIL;
+
+    uint64_t desc = DESC_EMPTY;
+    uint32_t card = 0;
+    if (mode == M_LANE_ARR) {
+        uint32_t c, r;
+        if (count || off == ALLOC_FAIL) {
+            lane_merge_arrays<false>(tbl, reinterpret_cast<const uint16_t *>(ca.p), ca.card,
+                                     reinterpret_cast<const uint16_t *>(cb.p), cb.card, c, r, nullptr);
+        } else {
+            lane_merge_arrays<true>(tbl, reinterpret_cast<const uint16_t *>(ca.p), ca.card,
+                                    reinterpret_cast<const uint16_t *>(cb.p), cb.card, c, r,
+                                    reinterpret_cast<uint16_t *>(es->arena + off));
+            if (c) {
+                const uint32_t ty = canon_type(c, r);
+                if (ty == T_RUN) {   // rare: rewrite the reserved space as runs
+                    uint32_t c2, r2;
+                    lane_sweep<true>(op, iv_src(ca), iv_src(cb), c2, r2, T_RUN, es->arena + off);
+                }
+                desc = mk_desc(c, ty, ty == T_RUN ? r : 0, off);
             }
+        }
+        card = c;
+    } else if (mode == M_LANE_SWEEP) {
+        if (count) {
+            uint32_t r;
+            lane_sweep<false>(op, iv_src(ca), iv_src(cb), card, r, 0, nullptr);
+        } else if (lc && off != ALLOC_FAIL) {
+            uint32_t c2, r2;
+            lane_sweep<true>(op, iv_src(ca), iv_src(cb), c2, r2, lt, es->arena + off);
             desc = mk_desc(lc, lt, lt == T_RUN ? lr : 0, off);
-            card_acc += lc;
-            words_acc += lbytes;
+            card = lc;
         }
-        ODESC[pos] = desc;
-        OKEY[pos] = (uint16_t)key;
-    } else if (kind == K_EMPTY) {
-        ODESC[pos] = DESC_EMPTY;
-        OKEY[pos] = (uint16_t)key;
+    } else if (mode == M_LANE_COPY && off != ALLOC_FAIL) {
+        const uint32_t *S = reinterpret_cast<const uint32_t *>(ca.p);
+        uint32_t *D = reinterpret_cast<uint32_t *>(es->arena + off);
+        for (uint32_t x = 0; x < bytes / 4; x++) D[x] = __ldg(S + x);
+        desc = mk_desc(ca.card, ca.type, ca.type == T_RUN ? ca.runs : 0, off);
+        card = ca.card;
     }
-    uint32_t lm = __ballot_sync(FULL, large);
-    while (lm) {
-        const int src = __ffs(lm) - 1;
-        lm &= lm - 1;
-        const uint32_t k_s = __shfl_sync(FULL, kind, src);
-        const uint32_t pos_s = __shfl_sync(FULL, pos, src);
-        const uint32_t key_s = __shfl_sync(FULL, key, src);
-        const uint64_t da_s = __shfl_sync(FULL, da, src), db_s = __shfl_sync(FULL, db, src);
-        uint64_t desc;
-        if (k_s == K_PAIR) desc = warp_pair(es, op, cref(A.base, da_s), cref(B.base, db_s), T0, T1, lane);
-        else desc = warp_copy(es, k_s == K_COPY_A ? cref(A.base, da_s) : cref(B.base, db_s), lane);
-        if (lane == 0) {
-            ODESC[pos_s] = desc;
-            OKEY[pos_s] = (uint16_t)key_s;
-            if (desc != DESC_EMPTY) {
-                card_acc += d_card(desc);
-                if (d_type(desc) == T_BITSET) bits_acc++;
-                else words_acc += word_alloc_bytes(d_type(desc), d_card(desc), d_runs(desc));
+    // warp-sized items, one at a time
+    uint32_t wq = __ballot_sync(FULL, mode == M_WARP_ARR || mode == M_WARP_COPY);
+    while (wq) {
+        const int src = __ffs(wq) - 1;
+        wq &= wq - 1;
+        const uint32_t m_s = __shfl_sync(FULL, mode, src), tbl_s = __shfl_sync(FULL, tbl, src);
+        const uint64_t off_s = __shfl_sync(FULL, count ? ALLOC_FAIL : off, src);
+        const unsigned long long pa_s = __shfl_sync(FULL, (unsigned long long)ca.p, src);
+        const unsigned long long pb_s = __shfl_sync(FULL, (unsigned long long)cb.p, src);
+        const uint32_t na_s = __shfl_sync(FULL, ca.card, src), nb_s = __shfl_sync(FULL, cb.card, src);
+        const uint32_t by_s = __shfl_sync(FULL, bytes, src);
+        uint64_t dsc = DESC_EMPTY;
+        uint32_t c = 0;
+        if (m_s == M_WARP_ARR) {
+            dsc = warp_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s), na_s,
+                                    reinterpret_cast<const uint16_t *>(pb_s), nb_s, stg, lane, off_s, c);
+        } else if (off_s != ALLOC_FAIL) {
+            const uint32_t *S = reinterpret_cast<const uint32_t *>(pa_s);
+            uint32_t *D = reinterpret_cast<uint32_t *>(es->arena + off_s);
+            for (uint32_t x = lane; x < by_s / 4; x += 32) D[x] = __ldg(S + x);
+            __syncwarp();
+        }
+        if (lane == (uint32_t)src) {
+            if (m_s == M_WARP_ARR) {
+                desc = dsc;
+                card = c;
+            } else if (off_s != ALLOC_FAIL) {
+                desc = mk_desc(ca.card, ca.type, ca.type == T_RUN ? ca.runs : 0, off_s);
+                card = ca.card;
             }
         }
-        __syncwarp();
     }
-    const unsigned long long cs = warp_sum64(card_acc), ws = warp_sum64(words_acc), is = warp_sum64(inb);
-    const uint32_t bs = warp_sum(bits_acc), ms = __popc(__ballot_sync(FULL, matchedA));
-    if (lane == 0) {
-        PairStats *S = P.stats + p;
-        if (cs) atomicAdd(&S->card, cs);
-        if (ws) atomicAdd(&S->words, ws);
-        if (is) atomicAdd(&S->in_bytes, is);
-        if (bs) atomicAdd(&S->nbits, bs);
-        if (ms) atomicAdd(&S->m, ms);
+    // results, and per-query sums over the lanes of the same query
+    if (has && !count) {
+        es->descs[pd.pos_base + it.pos] = desc;
+        es->keys[pd.pos_base + it.pos] = (uint16_t)key;
+    }
+    const uint32_t words = (desc != DESC_EMPTY) ? word_alloc_bytes(d_type(desc), d_card(desc), d_runs(desc)) : 0;
+    const uint32_t grp = __match_any_sync(FULL, has ? it.p : 0xFFFFFFFFu);
+    const uint32_t csum = __reduce_add_sync(grp, card), wsum = __reduce_add_sync(grp, words);
+    if (has && lane == (uint32_t)(__ffs(grp) - 1)) {
+        if (csum) atomicAdd(&P.stats[it.p].card, (unsigned long long)csum);
+        if (wsum) atomicAdd(&P.stats[it.p].words, (unsigned long long)wsum);
+    }
+    if (has) {
+        bytes_acc += (mode == M_LANE_COPY || mode == M_WARP_COPY) ? in_payload_bytes(dx)
+                                                                  : in_payload_bytes(it.da) + in_payload_bytes(it.db);
+        if (desc != DESC_EMPTY) bytes_acc += payload_bytes(d_type(desc), d_card(desc), d_runs(desc)) + 10;
     }
 }
 
+__global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
+    __shared__ uint32_t s_win[LEAN_THREADS / 32][66];
+    __shared__ Item s_q[LEAN_THREADS / 32][QCAP];
+    __shared__ __align__(16) uint16_t s_stg[LEAN_THREADS / 32][2 * WARP_MERGE_MAX];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t qn = 0;
+    bool done = false;
+    unsigned long long bytes_acc = 0;
+    for (;;) {
+        while (qn < 32 && !done) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(&P.es->work, 1ull);
+            t = __shfl_sync(FULL, t, 0);
+            if (t >= P.n_tiles) {
+                done = true;
+                break;
+            }
+            resolve_tile(P, t, s_win[warp], s_q[warp], qn, bytes_acc, lane);
+        }
+        if (qn == 0) break;
+        const uint32_t take = qn < 32 ? qn : 32;
+        process_items(P, s_q[warp] + (qn - take), take, s_stg[warp], bytes_acc, lane);
+        qn -= take;
+        __syncwarp();
+    }
+    const unsigned long long tot = warp_sum64(bytes_acc);
+    if (lane == 0 && tot) atomicAdd(&P.es->lean_bytes, tot);
+}
+
+// ------------------------------------------------------------ heavy kernel
+
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) k_pairs(PairParams P) {
+__global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
     extern __shared__ __align__(16) uint64_t smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t *T0 = smem + (size_t)warp * 2048;
     uint64_t *T1 = T0 + 1024;
+    ExecState *es = P.es;
+    const unsigned long long n = min(es->defer_n, es->defer_cap);
     for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(&P.es->work, 1ull);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= P.n_tiles) break;
-        pair_tile(P, t, T0, T1, lane);
+        unsigned long long e = 0;
+        if (lane == 0) e = atomicAdd(&es->hwork, 1ull);
+        e = __shfl_sync(FULL, e, 0);
+        if (e >= n) break;
+        const Deferred D = es->defer[e];
+        const PairDev pd = P.pairs[D.p];
+        const BmView A = P.pool[pd.a], B = P.pool[pd.b];
+        const uint32_t kind = D.kind_key >> 16, key = D.kind_key & 0xFFFFu;
+        PairStats *S = P.stats + D.p;
+        if (pd.flags & F_COUNT) {
+            const uint32_t c = warp_count_and(cref(A.base, D.da), cref(B.base, D.db), T0, T1, lane);
+            if (lane == 0) {
+                const unsigned long long ib = in_payload_bytes(D.da) + in_payload_bytes(D.db);
+                if (c) atomicAdd(&S->card, (unsigned long long)c);
+                atomicAdd(&es->heavy_bytes, ib);
+            }
+            __syncwarp();
+            continue;
+        }
+        uint64_t desc;
+        unsigned long long ib;
+        if (kind == K_PAIR) {
+            desc = warp_pair(es, pd.op, cref(A.base, D.da), cref(B.base, D.db), T0, T1, lane);
+            ib = in_payload_bytes(D.da) + in_payload_bytes(D.db);
+        } else {
+            const uint64_t dx = kind == K_COPY_A ? D.da : D.db;
+            desc = warp_copy(es, cref(kind == K_COPY_A ? A.base : B.base, dx), lane);
+            ib = in_payload_bytes(dx);
+        }
+        if (lane == 0) {
+            es->descs[pd.pos_base + D.pos] = desc;
+            es->keys[pd.pos_base + D.pos] = (uint16_t)key;
+            if (desc != DESC_EMPTY) {
+                const uint32_t ty = d_type(desc), c = d_card(desc), r = d_runs(desc);
+                atomicAdd(&S->card, (unsigned long long)c);
+                if (ty == T_BITSET) atomicAdd(&S->nbits, 1u);
+                else atomicAdd(&S->words, (unsigned long long)word_alloc_bytes(ty, c, r));
+                ib += payload_bytes(ty, c, r) + 10;
+            }
+            atomicAdd(&es->heavy_bytes, ib);
+        }
+        __syncwarp();
     }
 }
 
-// drop empty results: in-place stream compaction of each query's slot range
-// (positions are already in key order), one block per query
+// drop empty results: in-place stream compaction of each query's output
+// range (positions are already in key order), one block per query
 __global__ void __launch_bounds__(512) k_compact(const PairDev *pairs, uint32_t n_pairs, PairStats *stats,
                                                  const ExecState *es) {
     __shared__ uint32_t s_w[16];
@@ -431,9 +775,9 @@ __global__ void __launch_bounds__(512) k_compact(const PairDev *pairs, uint32_t 
     for (uint32_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
         const PairDev pd = pairs[p];
         if (pd.flags & F_COUNT) continue;
-        const uint32_t n = pd.n_slots;   // every position of the slot range is written once
-        uint64_t *D = es->descs + pd.slot_base;
-        uint16_t *K = es->keys + pd.slot_base;
+        const uint32_t n = pd.n_pos;
+        uint64_t *D = es->descs + pd.pos_base;
+        uint16_t *K = es->keys + pd.pos_base;
         uint32_t out = 0;
         for (uint32_t c0 = 0; c0 < n; c0 += blockDim.x) {
             const uint32_t i = c0 + tid;
@@ -464,26 +808,19 @@ __global__ void __launch_bounds__(512) k_compact(const PairDev *pairs, uint32_t 
 
 // ------------------------------------------------------------ host side
 
-template <int W>
-void launch_pairs_w(const PairParams &P, int ctas_per_sm, cudaStream_t s) {
-    static bool attr = false;
-    const int smem = W * 16384;
-    if (!attr) {
-        cudaFuncSetAttribute(k_pairs<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
-    unsigned long long need = (P.n_tiles + W - 1) / W;
-    unsigned long long cap = (unsigned long long)sm_count() * (unsigned long long)ctas_per_sm;
-    unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min(need, cap));
-    k_pairs<W><<<grid, W * 32, smem, s>>>(P);
+void init_kernel_attrs() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_heavy<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 16384);
+    cudaFuncSetAttribute(k_heavy<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 16384);
+    cudaFuncSetAttribute(k_heavy<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 16384);
+    done = true;
 }
 
-void launch_pairs(const PairParams &P, const rb_schedule &sc, cudaStream_t s) {
-    switch (sc.warps_per_cta) {
-        case 2: launch_pairs_w<2>(P, sc.ctas_per_sm, s); break;
-        case 8: launch_pairs_w<8>(P, sc.ctas_per_sm, s); break;
-        default: launch_pairs_w<4>(P, sc.ctas_per_sm, s); break;
-    }
+template <int W>
+void launch_heavy_w(const PairParams &P, int ctas_per_sm, cudaStream_t s) {
+    const unsigned grid = (unsigned)std::max(1, sm_count() * ctas_per_sm);
+    k_heavy<W><<<grid, W * 32, W * 16384, s>>>(P);
 }
 
 }  // namespace
@@ -492,9 +829,9 @@ struct rb_plan {
     std::vector<const rb *> pool;
     std::vector<rb_query> q;
     std::vector<PairDev> pairs;
-    uint64_t total_slots = 0, total_tiles = 0;
-    uint64_t words_cap = 0, bits_cap = 0;   // arena sizes for the next run
-    bool exact = false;                     // caps measured by a previous run
+    uint64_t total_pos = 0, total_tiles = 0;
+    uint64_t words_cap = 0, bits_cap = 0, defer_cap = 0;   // arena sizes for the next run
+    bool exact = false;                                    // caps measured by a previous run
     bool any_mat = false;
     uint8_t *tables = nullptr;
     uint64_t tables_bytes = 0;
@@ -506,11 +843,11 @@ struct rb_plan {
     PairStats *h_stats = nullptr;
     ExecState *h_es = nullptr;
     cudaStream_t ps = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_in = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev_in = nullptr;
     cudaGraphExec_t gexec = nullptr;
     rb_schedule gsched = {0, 0, 0, 0};
-    double last_ms = 0;
-    uint64_t last_alg = 0, last_out = 0;
+    double last_ms = 0, last_lean_ms = 0, last_heavy_ms = 0;
+    uint64_t last_alg = 0, last_out = 0, last_lean_bytes = 0, last_heavy_bytes = 0, last_deferred = 0;
     cudaStream_t alloc_stream = nullptr;
 };
 
@@ -524,6 +861,7 @@ void plan_destroy(rb_plan *p) {
     if (p->h_es) cudaFreeHost(p->h_es);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->ev2) cudaEventDestroy(p->ev2);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ps) cudaStreamDestroy(p->ps);
     delete p;
@@ -558,7 +896,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     p->q.assign(q, q + nq);
     p->pairs.resize(nq);
     std::vector<unsigned long long> tb(nq + 1);
-    uint64_t slots = 0, tiles = 0, ew = 0, eb = 0, bw = 0, bb = 0;
+    uint64_t npos = 0, tiles = 0, ew = 0, eb = 0, bw = 0, bb = 0, ed = 0;
     for (uint64_t i = 0; i < nq; i++) {
         const rb_query &x = q[i];
         if (x.op > 3 || x.a >= pool_n || x.b >= pool_n) {
@@ -571,16 +909,29 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
         d.a = x.a;
         d.b = x.b;
         d.op = x.op;
-        d.flags = (x.flags & RB_Q_COUNT_ONLY) ? F_COUNT : 0;
-        uint64_t ns;
-        if ((d.flags & F_COUNT) || x.op == OP_AND) ns = std::min(A->n, B->n);
-        else if (x.op == OP_ANDNOT) ns = A->n;
-        else ns = (uint64_t)A->n + B->n;
+        const bool count = (x.flags & RB_Q_COUNT_ONLY) != 0;
+        const uint64_t na = A->n, nb = B->n, mn = std::min(na, nb), mx = std::max(na, nb);
+        // merge mode unless one key list is more than 8 times the other
+        // (then a binary search per key of the smaller side is cheaper)
+        bool merge;
+        if (!count && (x.op == OP_OR || x.op == OP_XOR)) merge = true;
+        else if (!count && x.op == OP_ANDNOT) merge = !(nb * 8 < na || na * 8 < nb);
+        else merge = mx <= 8 * mn;
+        d.flags = (count ? F_COUNT : 0) | (merge ? F_MERGE : 0);
+        uint64_t ns, np;
+        if (merge) ns = na + nb;
+        else if (count || x.op == OP_AND) ns = mn;
+        else ns = na;
+        if (count) np = 0;
+        else if (x.op == OP_OR || x.op == OP_XOR) np = na + nb;
+        else if (x.op == OP_ANDNOT) np = na;
+        else np = merge ? na : mn;
         d.n_slots = (uint32_t)ns;
-        d.pad = 0;
-        d.slot_base = (d.flags & F_COUNT) ? 0 : slots;
-        if (!(d.flags & F_COUNT)) {
-            slots += ns;
+        d.n_pos = (uint32_t)np;
+        d.pos_base = npos;
+        npos += np;
+        ed += 2ull * (A->n_bitsets + B->n_bitsets) + ns / 16;
+        if (!count) {
             p->any_mat = true;
             uint64_t w1, b1;
             query_bounds(A, B, x.op, w1, b1);
@@ -601,8 +952,9 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
         tiles += (ns + 31) / 32;
     }
     tb[nq] = tiles;
-    p->total_slots = slots;
+    p->total_pos = npos;
     p->total_tiles = tiles;
+    p->defer_cap = std::max<uint64_t>(ed, 4096);
     if (use_bounds) {
         p->words_cap = bw;
         p->bits_cap = bb;
@@ -624,7 +976,6 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     p->d_tile_base = (unsigned long long *)(p->tables + o_tb);
     p->d_stats = (PairStats *)(p->tables + o_stats);
     p->d_es = (ExecState *)(p->tables + o_es);
-    // host staging: pool views, then everything goes up in one copy
     std::vector<uint8_t> hbuf(o_stats);
     BmView *hv = (BmView *)(hbuf.data() + o_pool);
     for (uint32_t i = 0; i < pool_n; i++) hv[i] = view_of(pool[i]);
@@ -636,6 +987,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev2);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         plan_destroy(p);
@@ -645,9 +997,9 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     return RB_OK;
 }
 
-// the launch sequence of one run, enqueued on stream s
-// capture: the events become external event-record nodes of the graph, so
-// the kernel's time can still be read after a replay
+// the launch sequence of one run, enqueued on stream s; when captured, the
+// events become external event-record nodes so the kernel times can still
+// be read after a graph replay
 cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool capture) {
     const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
     const uint64_t nq = p->q.size();
@@ -663,10 +1015,27 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     P.n_tiles = p->total_tiles;
     P.n_pairs = (uint32_t)nq;
     P.small_iv = sc.small_intervals;
+    init_kernel_attrs();
     if ((e = cudaEventRecordWithFlags(p->ev0, s, evf)) != cudaSuccess) return e;
-    if (p->total_tiles) launch_pairs(P, sc, s);
+    if (p->total_tiles) {
+        const unsigned long long lean_cap =
+            (unsigned long long)sm_count() * (sc.lean_ctas_per_sm ? sc.lean_ctas_per_sm : 8) * (LEAN_THREADS / 32);
+        const unsigned long long warps = std::min<unsigned long long>(P.n_tiles, lean_cap);
+        const unsigned grid =
+            (unsigned)std::max<unsigned long long>(1, (warps + LEAN_THREADS / 32 - 1) / (LEAN_THREADS / 32));
+        k_lean<<<grid, LEAN_THREADS, 0, s>>>(P);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaEventRecordWithFlags(p->ev1, s, evf)) != cudaSuccess) return e;
+    if (p->total_tiles) {
+        switch (sc.warps_per_cta) {
+            case 2: launch_heavy_w<2>(P, sc.ctas_per_sm, s); break;
+            case 8: launch_heavy_w<8>(P, sc.ctas_per_sm, s); break;
+            default: launch_heavy_w<4>(P, sc.ctas_per_sm, s); break;
+        }
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaEventRecordWithFlags(p->ev2, s, evf)) != cudaSuccess) return e;
     if (p->any_mat) {
         unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nq, (uint64_t)sm_count() * 8));
         k_compact<<<grid, 512, 0, s>>>(p->d_pairs, (uint32_t)nq, p->d_stats, p->d_es);
@@ -677,41 +1046,47 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     return e;
 }
 
-// one run with the plan's current caps; on success *arena holds the results
-// (NULL when every query is count-only); *overflow tells the caller to retry
+struct ArenaLayout {
+    uint64_t o_keys, o_defer, o_words, o_bits, bytes;
+};
+ArenaLayout arena_layout(const rb_plan *p) {
+    ArenaLayout L;
+    const uint64_t T = p->total_pos;
+    L.o_keys = align_up(8 * T, 256);
+    L.o_defer = align_up(L.o_keys + 2 * T, 256);
+    L.o_words = align_up(L.o_defer + sizeof(Deferred) * p->defer_cap, 256);
+    L.o_bits = align_up(L.o_words + p->words_cap, 256);
+    L.bytes = L.o_bits + p->bits_cap;
+    return L;
+}
+
+// one run with the plan's current caps; on success *arena holds the results;
+// *overflow tells the caller to retry with the exact sizes now recorded
 rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool *overflow) {
     *arena = nullptr;
     *overflow = false;
     const rb_schedule sc = current_schedule();
-    const uint64_t T = p->total_slots;
-    const uint64_t o_keys = align_up(8 * T, 256);
-    const uint64_t o_words = align_up(o_keys + 2 * T, 256);
-    const uint64_t o_bits = align_up(o_words + p->words_cap, 256);
-    const uint64_t bytes = o_bits + p->bits_cap;
-    if (p->any_mat && bytes >= MAX_OFFSET)
+    const ArenaLayout L = arena_layout(p);
+    if (L.bytes >= MAX_OFFSET)
         return set_err(RB_ERANGE, "batch results need %llu bytes, above the 128 GiB descriptor reach; split the batch",
-                       (unsigned long long)bytes);
-    RbArena *a = nullptr;
-    if (p->any_mat) {
-        a = arena_new(bytes, s);
-        if (!a) return RB_ENOMEM;
-    }
+                       (unsigned long long)L.bytes);
+    RbArena *a = arena_new(L.bytes, s);
+    if (!a) return RB_ENOMEM;
     ExecState &h = *p->h_es;
     memset(&h, 0, sizeof h);
-    if (a) {
-        h.arena = (uint8_t *)a->ptr;
-        h.descs = (uint64_t *)a->ptr;
-        h.keys = (uint16_t *)((uint8_t *)a->ptr + o_keys);
-        h.words_off = o_words;
-        h.words_cap = p->words_cap;
-        h.bits_off = o_bits;
-        h.bits_cap = p->bits_cap;
-    }
+    h.arena = (uint8_t *)a->ptr;
+    h.descs = (uint64_t *)a->ptr;
+    h.keys = (uint16_t *)((uint8_t *)a->ptr + L.o_keys);
+    h.defer = (Deferred *)((uint8_t *)a->ptr + L.o_defer);
+    h.defer_cap = p->defer_cap;
+    h.words_off = L.o_words;
+    h.words_cap = p->words_cap;
+    h.bits_off = L.o_bits;
+    h.bits_cap = p->bits_cap;
     cudaError_t e = cudaSuccess;
     if (graph) {
         if (!p->ps) e = cudaStreamCreateWithFlags(&p->ps, cudaStreamNonBlocking);
-        if (e == cudaSuccess && p->gexec &&
-            memcmp(&p->gsched, &sc, sizeof sc) != 0) {
+        if (e == cudaSuccess && p->gexec && memcmp(&p->gsched, &sc, sizeof sc) != 0) {
             cudaGraphExecDestroy(p->gexec);
             p->gexec = nullptr;
         }
@@ -739,22 +1114,33 @@ rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool
         arena_unref(a);
         return cuda_err(e, "batch run");
     }
-    float ms = 0.f;
-    if (p->total_tiles && cudaEventElapsedTime(&ms, p->ev0, p->ev1) == cudaSuccess) p->last_ms = ms;
-    else p->last_ms = 0;
-    cudaGetLastError();
-    if (h.status & 1u) {
+    float m1 = 0.f, m2 = 0.f;
+    if (p->total_tiles && cudaEventElapsedTime(&m1, p->ev0, p->ev1) == cudaSuccess &&
+        cudaEventElapsedTime(&m2, p->ev1, p->ev2) == cudaSuccess) {
+        p->last_lean_ms = m1;
+        p->last_heavy_ms = m2;
+        p->last_ms = m1 + m2;
+    } else {
+        p->last_ms = p->last_lean_ms = p->last_heavy_ms = 0;
+    }
+    clear_stale_error();
+    if (h.status & 3u) {
         *overflow = true;
-        p->words_cap = h.words_used;
-        p->bits_cap = h.bits_used;
+        p->words_cap = std::max<uint64_t>(p->words_cap, h.words_used);
+        p->bits_cap = std::max<uint64_t>(p->bits_cap, h.bits_used);
+        p->defer_cap = std::max<uint64_t>(p->defer_cap, h.defer_n);
         arena_unref(a);
         return RB_OK;
     }
     if (!p->exact) {
         p->words_cap = h.words_used;
         p->bits_cap = h.bits_used;
+        p->defer_cap = std::max<uint64_t>(h.defer_n, 1);
         p->exact = true;
     }
+    p->last_lean_bytes = h.lean_bytes;
+    p->last_heavy_bytes = h.heavy_bytes;
+    p->last_deferred = h.defer_n;
     *arena = a;
     return RB_OK;
 }
@@ -765,20 +1151,18 @@ rb_status plan_execute(rb_plan *p, rb_t **outs, uint64_t *counts, cudaStream_t s
     bool overflow = false;
     rb_status st = RB_OK;
     for (int attempt = 0; attempt < 3; attempt++) {
-        st = run_once(p, s, graph && attempt > 0 ? false : graph, &a, &overflow);
+        st = run_once(p, s, attempt == 0 ? graph : false, &a, &overflow);
         if (st != RB_OK) return st;
         if (!overflow) break;
     }
     if (overflow) return set_err(RB_ENOMEM, "batch: output arena overflow persisted");
     const uint64_t nq = p->q.size();
-    const uint64_t T = p->total_slots;
-    const uint64_t o_keys = align_up(8 * T, 256);
+    const ArenaLayout L = arena_layout(p);
     uint64_t alg = 0, outb = 0;
     for (uint64_t i = 0; i < nq; i++) {
         const PairDev &d = p->pairs[i];
         const PairStats &S = p->h_stats[i];
         const rb *A = p->pool[d.a], *B = p->pool[d.b];
-        alg += S.in_bytes;
         if (d.flags & F_COUNT) {
             const uint64_t inter = S.card;
             uint64_t v;
@@ -789,13 +1173,10 @@ rb_status plan_execute(rb_plan *p, rb_t **outs, uint64_t *counts, cudaStream_t s
                 default: v = A->card + B->card - 2 * inter; break;
             }
             if (counts) counts[i] = v;
-            alg += 8;
             if (outs) outs[i] = nullptr;
             continue;
         }
-        const uint64_t ob = S.words + 8192ull * S.nbits + 10ull * S.n_out;
-        alg += ob;
-        outb += ob;
+        outb += S.words + 8192ull * S.nbits + 10ull * S.n_out;
         if (counts) counts[i] = S.card;
         if (outs) {
             rb *h = handle_new();
@@ -804,14 +1185,14 @@ rb_status plan_execute(rb_plan *p, rb_t **outs, uint64_t *counts, cudaStream_t s
             h->word_bytes = S.words;
             h->n_bitsets = S.nbits;
             h->base = (uint8_t *)a->ptr;
-            h->descs = (uint64_t *)a->ptr + d.slot_base;
-            h->keys = (uint16_t *)((uint8_t *)a->ptr + o_keys) + d.slot_base;
+            h->descs = (uint64_t *)a->ptr + d.pos_base;
+            h->keys = (uint16_t *)((uint8_t *)a->ptr + L.o_keys) + d.pos_base;
             h->arena = a;
             arena_ref(a);
             outs[i] = h;
         }
     }
-    p->last_alg = alg;
+    p->last_alg = alg + p->h_es->lean_bytes + p->h_es->heavy_bytes;
     p->last_out = outb;
     arena_unref(a);
     return RB_OK;
@@ -927,11 +1308,15 @@ rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream)
     return plan_execute(p, outs, counts, (cudaStream_t)stream, p->exact);
 }
 
-rb_status rb_plan_stats(const rb_plan_t *p, double *kernel_ms, uint64_t *alg_bytes, uint64_t *out_bytes) {
-    if (!p) return set_err(RB_EINVAL, "rb_plan_stats: NULL plan");
-    if (kernel_ms) *kernel_ms = p->last_ms;
-    if (alg_bytes) *alg_bytes = p->last_alg;
-    if (out_bytes) *out_bytes = p->last_out;
+rb_status rb_plan_stats(const rb_plan_t *p, rb_plan_timing *t) {
+    if (!p || !t) return set_err(RB_EINVAL, "rb_plan_stats: NULL argument");
+    t->lean_ms = p->last_lean_ms;
+    t->heavy_ms = p->last_heavy_ms;
+    t->lean_bytes = p->last_lean_bytes;
+    t->heavy_bytes = p->last_heavy_bytes;
+    t->alg_bytes = p->last_alg;
+    t->out_bytes = p->last_out;
+    t->deferred = p->last_deferred;
     return RB_OK;
 }
 
@@ -942,26 +1327,29 @@ rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *be
     if (reps == 0) reps = 1;
     cudaStream_t s = (cudaStream_t)stream;
     const rb_schedule saved = current_schedule();
-    static const uint32_t shapes[][2] = {{2, 6}, {4, 3}, {8, 1}};
-    static const uint32_t smalls[] = {8, 32, 128, 512};
+    static const uint32_t heavy[][2] = {{2, 6}, {4, 3}, {8, 1}};
+    static const uint32_t smalls[] = {64, 256, 512};
+    static const uint32_t leans[] = {4, 8};
     rb_schedule win = saved;
     double win_ms = 1e30;
     std::vector<rb_t *> outs(p->q.size(), nullptr);
-    for (auto &sh : shapes) {
+    for (auto &sh : heavy) {
         for (uint32_t sm : smalls) {
-            rb_schedule c = {sh[0], sh[1], sm, 0};
-            if (rb_set_schedule(&c) != RB_OK) continue;
-            double tot = 0;
-            bool ok = true;
-            for (uint32_t r = 0; r < reps + 1 && ok; r++) {
-                rb_status st = plan_execute(p, outs.data(), nullptr, s, false);
-                for (auto &h : outs) { rb_free(h); h = nullptr; }
-                if (st != RB_OK) ok = false;
-                else if (r > 0) tot += p->last_ms;   // first run is a warm-up
-            }
-            if (ok && tot / reps < win_ms) {
-                win_ms = tot / reps;
-                win = c;
+            for (uint32_t ln : leans) {
+                rb_schedule c = {sh[0], sh[1], sm, ln};
+                if (rb_set_schedule(&c) != RB_OK) continue;
+                double tot = 0;
+                bool ok = true;
+                for (uint32_t r = 0; r < reps + 1 && ok; r++) {
+                    rb_status st = plan_execute(p, outs.data(), nullptr, s, false);
+                    for (auto &h : outs) { rb_free(h); h = nullptr; }
+                    if (st != RB_OK) ok = false;
+                    else if (r > 0) tot += p->last_ms;   // the first run is a warm-up
+                }
+                if (ok && tot / reps < win_ms) {
+                    win_ms = tot / reps;
+                    win = c;
+                }
             }
         }
     }
