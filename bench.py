@@ -112,55 +112,64 @@ def make_workload(seed_offset=0, args=None):
     return pool, ops, a, b
 
 
-def cpu_oracle_leg(pool, ops, a, b, budget_s=15.0, threads=None):
-    """Time the oracle (as it stands) on the host cores over a bounded sample
-    of the pairs: the materialised op plus the Jaccard counts of each pair."""
-    import oracle
-    oracle.build()
-    threads = threads or os.cpu_count() or 1
-    sizes = pool.sizes()
-    order = np.arange(len(ops))
-    # build the oracle bitmaps of a prefix of the pairs (not timed)
-    sample = []
-    need = set()
-    est_vals = 0
-    for i in order:
-        sample.append(int(i))
-        need.update([int(a[i]), int(b[i])])
-        est_vals += int(sizes[a[i]]) + int(sizes[b[i]])
-        if est_vals > 3e8 or len(sample) >= 2048:
-            break
-    with cf.ThreadPoolExecutor(threads) as ex:
-        built = dict(zip(sorted(need), ex.map(lambda j: oracle.Bitmap.from_sorted(pool.values(j)), sorted(need))))
+class OracleSample:
+    """The CPU oracle (as it stands, test infrastructure) over a bounded
+    sample of the pairs: its bitmaps are built once (untimed), then time()
+    runs the materialised op plus the Jaccard counts of each pair on the host
+    cores, pairs spread over a thread pool (ctypes releases the GIL)."""
 
-    def one(i):
-        A, B = built[int(a[i])], built[int(b[i])]
-        r = A.op(int(ops[i]), B)
-        c = r.card
+    def __init__(self, pool, ops, a, b, sample_values=3e9, threads=None):
+        import oracle
+        oracle.build()
+        self.threads = threads or os.cpu_count() or 1
+        self.sizes = pool.sizes()
+        self.ops, self.a, self.b, self.n_total = ops, a, b, len(ops)
+        self.sample, need, est = [], set(), 0
+        for i in range(len(ops)):
+            self.sample.append(i)
+            need.update([int(a[i]), int(b[i])])
+            est += int(self.sizes[a[i]]) + int(self.sizes[b[i]])
+            if est > sample_values or len(self.sample) >= 4096:
+                break
+        need = sorted(need)
+        with cf.ThreadPoolExecutor(self.threads) as ex:
+            self.built = dict(zip(need, ex.map(lambda j: oracle.Bitmap.from_sorted(pool.values(j)), need)))
+
+    def _one(self, i):
+        A, B = self.built[int(self.a[i])], self.built[int(self.b[i])]
+        r = A.op(int(self.ops[i]), B)
         r.close()
         A.jaccard(B)
-        return int(sizes[a[i]]) + int(sizes[b[i]]), c
+        return int(self.sizes[self.a[i]]) + int(self.sizes[self.b[i]])
 
-    done_vals, done_pairs = 0, 0
-    t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(threads) as ex:
-        futs = []
-        for i in sample:
-            futs.append(ex.submit(one, i))
-        for f in futs:
-            v, _ = f.result()
-            done_vals += v
-            done_pairs += 1
-            if time.perf_counter() - t0 > budget_s:
-                for g in futs:
-                    g.cancel()
-                break
-    dt = time.perf_counter() - t0
-    for x in built.values():
-        x.close()
-    return {"value": done_vals / dt / 1e9, "unit": "Gints/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {done_pairs} of the {len(ops)} pairs (materialised op + Jaccard each), "
-                      f"{done_vals:,} input values, {dt:.1f}s on {threads} host threads"}
+    def time(self, budget_s):
+        done_vals, done_pairs = 0, 0
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(self.threads) as ex:
+            futs = [ex.submit(self._one, i) for i in self.sample]
+            for f in futs:
+                done_vals += f.result()
+                done_pairs += 1
+                if time.perf_counter() - t0 > budget_s:
+                    for g in futs:
+                        g.cancel()
+                    break
+        dt = time.perf_counter() - t0
+        return {"value": done_vals / dt / 1e9, "unit": "Gints/s", "cores": self.threads, "kind": "oracle",
+                "sample": f"first {done_pairs} of the {self.n_total} pairs (materialised op + Jaccard each), "
+                          f"{done_vals:,} input values, {dt:.1f}s on {self.threads} host threads"}
+
+    def close(self):
+        for x in self.built.values():
+            x.close()
+
+
+def cpu_oracle_leg(pool, ops, a, b, budget_s=15.0):
+    s = OracleSample(pool, ops, a, b)
+    try:
+        return s.time(budget_s)
+    finally:
+        s.close()
 
 
 def run_reference(args):
@@ -168,12 +177,14 @@ def run_reference(args):
     if rank != 0:
         return 0
     pool, ops, a, b = make_workload(args=args)
+    sample = OracleSample(pool, ops, a, b)
     steps = []
     res = None
     for s in range(args.warmup + args.steps):
-        res = cpu_oracle_leg(pool, ops, a, b, budget_s=args.ref_budget)
+        res = sample.time(args.ref_budget)
         if s >= args.warmup:
             steps.append(res["value"])
+    sample.close()
     value = statistics.median(steps)
     line = {"impl": "reference", "metric": "batched Roaring AND/OR Gints/s", "value": value, "unit": "Gints/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
@@ -282,6 +293,8 @@ def run_ours(args):
                 o.free()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t1) / e2e_steps
+
+    bitset_legs = {} if args.no_subsets else bitset_subset_legs(rb, G, pool, sizes)
     h2d = 2 * (32 * len(G) + 32 * n_pairs + 8 * (n_pairs + 1) + 128) + 2 * 16 * n_pairs
     d2h = 2 * (40 * n_pairs + 128) + 8 * n_pairs * 4
     e2e = {"value": units / e2e_s / 1e9, "unit": "Gints/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -329,11 +342,65 @@ def run_ours(args):
             "gpu_launches": 5 * args.steps,
             "clocks": clk,
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
-            "per_pair": per}
+            "per_pair": per, "bitset_and_or": bitset_legs}
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bitset_subset_legs(rb, G, pool, sizes, n_pairs=16384, reps=5):
+    """Bitset-dominated AND/OR: pairs of dense-clustered pool bitmaps (ops AND
+    and OR, 50/50), (1) drawn uniformly, (2) drawn among pairs whose key
+    ranges overlap, so that bitset x bitset pairs are actually combined."""
+    peak, _ = measured_peaks()
+    rng = np.random.default_rng(44)
+    dense = np.array([i for i in range(pool.n) if pool.klass(i) == 1])
+    kmin = np.array([int(pool.values(i)[0]) >> 16 for i in dense])
+    kmax = np.array([int(pool.values(i)[-1]) >> 16 for i in dense])
+    order = np.argsort(kmin)
+    over = []
+    for x in range(len(order)):
+        i = order[x]
+        for y in range(x + 1, len(order)):
+            j = order[y]
+            if kmin[j] > kmax[i]:
+                break
+            over.append((dense[i], dense[j]))
+    over = np.array(over, dtype=np.uint32).reshape(-1, 2)
+    out = {}
+    sets = {"uniform": (rng.choice(dense, n_pairs), rng.choice(dense, n_pairs))}
+    if len(over):
+        pick = over[rng.choice(len(over), n_pairs)]
+        sets["overlapping"] = (pick[:, 0], pick[:, 1])
+    for name, (a, b) in sets.items():
+        keep = a != b
+        a, b = a[keep].astype(np.uint32), b[keep].astype(np.uint32)
+        ops = rng.integers(0, 2, len(a)).astype(np.uint32)
+        plan = rb.Plan(G, ops, a, b)
+        stats = []
+        for r in range(3 + reps):
+            outs, _ = plan.run()
+            st = plan.stats()
+            for o in outs:
+                if o is not None:
+                    o.free()
+            if r >= 3:
+                stats.append(st)
+        plan.free()
+        hms = statistics.mean(s["heavy_ms"] for s in stats)
+        lms = statistics.mean(s["lean_ms"] for s in stats)
+        hb = statistics.mean(s["heavy_bytes"] for s in stats)
+        lb = statistics.mean(s["lean_bytes"] for s in stats)
+        units = float((sizes[a] + sizes[b]).sum())
+        out[name] = {"pairs": int(len(a)), "gints_s": units / ((hms + lms) / 1e3) / 1e9,
+                     "k_heavy": {"ms": hms, "alg_bytes": hb, "achieved_gbs": hb / hms / 1e6,
+                                 "frac": hb / hms / 1e6 / peak},
+                     "pair_stage": {"ms": hms + lms, "alg_bytes": hb + lb,
+                                    "achieved_gbs": (hb + lb) / (hms + lms) / 1e6,
+                                    "frac": (hb + lb) / (hms + lms) / 1e6 / peak},
+                     "deferred_pairs": statistics.mean(s["deferred"] for s in stats)}
+    return out
 
 
 def per_pair_leg(rb, G, ops, a, b, sizes, n=512):
@@ -367,8 +434,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-subsets", action="store_true", help="skip the bitset-dominated AND/OR legs")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--ref-budget", type=float, default=10.0)
+    ap.add_argument("--ref-budget", type=float, default=5.0, help="seconds of oracle work per reference step")
     ap.add_argument("--per-pair-sample", type=int, default=512)
     ap.add_argument("--pool", type=int, default=0, help="scaled case: number of pool bitmaps (profiling)")
     ap.add_argument("--pairs", type=int, default=0, help="scaled case: number of pairs (profiling)")

@@ -711,26 +711,144 @@ __global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
 
 // ------------------------------------------------------------ heavy kernel
 
+// bulk-copy state of one heavy-kernel warp
+struct Tma {
+    uint64_t *bar;
+    uint32_t phase;
+    bool failed;
+};
+
+// a wait ran out: record it, give the copy in flight one more bounded wait,
+// and stop using the tiles
+__device__ bool tma_fail(Tma &t, ExecState *es, uint32_t lane) {
+    if (lane == 0) atomicOr(&es->status, 4u);
+    mbar_wait(t.bar, t.phase ^ 1u);
+    t.failed = true;
+    return false;
+}
+
+// Stage both operands of a pair in the warp's tiles: bitsets arrive by bulk
+// copy (a -> T0, b -> T1) while the warp expands array and run operands into
+// the other tile.  False if a wait ran out.
+__device__ bool stage_pair(const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1, Tma &t, ExecState *es,
+                           uint32_t lane) {
+    const uint32_t nbits = (a.type == T_BITSET) + (b.type == T_BITSET);
+    if (nbits) {
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+            mbar_expect_tx(t.bar, nbits * 8192u);
+            if (a.type == T_BITSET) bulk_load(T0, a.p, 8192u, t.bar);
+            if (b.type == T_BITSET) bulk_load(T1, b.p, 8192u, t.bar);
+        }
+    }
+    if (a.type != T_BITSET) t_decode(T0, a, lane);
+    if (b.type != T_BITSET) t_decode(T1, b, lane);
+    if (nbits) {
+        const bool ok = mbar_wait(t.bar, t.phase);
+        t.phase ^= 1u;
+        if (!ok) return tma_fail(t, es, lane);
+    }
+    return true;
+}
+
+// write tile T0 as a bitset container with one bulk store
+__device__ uint64_t store_bitset_tile(ExecState *es, const uint64_t *T0, uint32_t c, uint32_t lane) {
+    const uint64_t off = alloc_bitset_warp(es, lane);
+    if (off == ALLOC_FAIL) return DESC_EMPTY;
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+        bulk_store(es->arena + off, T0, 8192u);
+        bulk_wait_read();
+    }
+    __syncwarp();
+    return mk_desc(c, T_BITSET, 0, off);
+}
+
+// a op b for one deferred container pair
+__device__ uint64_t heavy_pair(ExecState *es, uint32_t op, const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1,
+                               Tma &t, uint32_t lane) {
+    const bool a_arr = a.type == T_ARRAY, b_arr = b.type == T_ARRAY;
+    if ((op == OP_AND && (a_arr || b_arr)) || (op == OP_ANDNOT && a_arr))
+        return warp_pair(es, op, a, b, T0, T1, lane);   // bit probes of an array's values
+    if (!stage_pair(a, b, T0, T1, t, es, lane)) return DESC_EMPTY;
+    uint32_t c, r;
+    t_combine<true>(T0, T0, T1, op, c, r, lane);
+    __syncwarp();
+    if (c == 0) return DESC_EMPTY;
+    const uint32_t ty = canon_type(c, r);
+    if (ty == T_BITSET) return store_bitset_tile(es, T0, c, lane);
+    const uint64_t off = alloc_words_warp(es, word_alloc_bytes(ty, c, r), lane);
+    if (off == ALLOC_FAIL) return DESC_EMPTY;
+    if (ty == T_ARRAY) {
+        t_emit_array(T0, reinterpret_cast<uint16_t *>(es->arena + off), lane);
+    } else {
+        uint16_t *S = reinterpret_cast<uint16_t *>(T1);
+        t_emit_runs(T0, S, S + 2048, reinterpret_cast<uint32_t *>(es->arena + off), r, lane);
+    }
+    __syncwarp();
+    return mk_desc(c, ty, ty == T_RUN ? r : 0, off);
+}
+
+// copy of a deferred container: bitsets through shared memory by bulk copy
+__device__ uint64_t heavy_copy(ExecState *es, const CRef &x, uint64_t *T0, uint64_t *T1, Tma &t, uint32_t lane) {
+    if (x.type != T_BITSET) return warp_copy(es, x, lane);
+    (void)T1;
+    fence_proxy_async();
+    __syncwarp();
+    if (lane == 0) {
+        mbar_expect_tx(t.bar, 8192u);
+        bulk_load(T0, x.p, 8192u, t.bar);
+    }
+    const bool ok = mbar_wait(t.bar, t.phase);
+    t.phase ^= 1u;
+    if (!ok) {
+        tma_fail(t, es, lane);
+        return DESC_EMPTY;
+    }
+    return store_bitset_tile(es, T0, x.card, lane);
+}
+
+// |a n b| for one deferred container pair
+__device__ uint32_t heavy_count(const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1, Tma &t, ExecState *es,
+                                uint32_t lane) {
+    if (a.type == T_ARRAY || b.type == T_ARRAY) return warp_count_and(a, b, T0, T1, lane);
+    if (!stage_pair(a, b, T0, T1, t, es, lane)) return 0;
+    uint32_t c, r;
+    t_combine<false>(nullptr, T0, T1, OP_AND, c, r, lane);
+    __syncwarp();
+    return c;
+}
+
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
     extern __shared__ __align__(16) uint64_t smem[];
+    __shared__ __align__(8) uint64_t s_bar[WARPS];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t *T0 = smem + (size_t)warp * 2048;
     uint64_t *T1 = T0 + 1024;
     ExecState *es = P.es;
+    if (lane == 0) mbar_init(&s_bar[warp], 1);
+    fence_mbar_init();
+    __syncwarp();
+    Tma t;
+    t.bar = &s_bar[warp];
+    t.phase = 0;
+    t.failed = false;
     const unsigned long long n = min(es->defer_n, es->defer_cap);
     for (;;) {
         unsigned long long e = 0;
         if (lane == 0) e = atomicAdd(&es->hwork, 1ull);
         e = __shfl_sync(FULL, e, 0);
-        if (e >= n) break;
+        if (e >= n || t.failed) break;
         const Deferred D = es->defer[e];
         const PairDev pd = P.pairs[D.p];
         const BmView A = P.pool[pd.a], B = P.pool[pd.b];
         const uint32_t kind = D.kind_key >> 16, key = D.kind_key & 0xFFFFu;
         PairStats *S = P.stats + D.p;
         if (pd.flags & F_COUNT) {
-            const uint32_t c = warp_count_and(cref(A.base, D.da), cref(B.base, D.db), T0, T1, lane);
+            const uint32_t c = heavy_count(cref(A.base, D.da), cref(B.base, D.db), T0, T1, t, es, lane);
             if (lane == 0) {
                 const unsigned long long ib = in_payload_bytes(D.da) + in_payload_bytes(D.db);
                 if (c) atomicAdd(&S->card, (unsigned long long)c);
@@ -742,11 +860,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
         uint64_t desc;
         unsigned long long ib;
         if (kind == K_PAIR) {
-            desc = warp_pair(es, pd.op, cref(A.base, D.da), cref(B.base, D.db), T0, T1, lane);
+            desc = heavy_pair(es, pd.op, cref(A.base, D.da), cref(B.base, D.db), T0, T1, t, lane);
             ib = in_payload_bytes(D.da) + in_payload_bytes(D.db);
         } else {
             const uint64_t dx = kind == K_COPY_A ? D.da : D.db;
-            desc = warp_copy(es, cref(kind == K_COPY_A ? A.base : B.base, dx), lane);
+            desc = heavy_copy(es, cref(kind == K_COPY_A ? A.base : B.base, dx), T0, T1, t, lane);
             ib = in_payload_bytes(dx);
         }
         if (lane == 0) {
@@ -763,6 +881,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
         }
         __syncwarp();
     }
+    // every bulk store of this warp has completed before the kernel ends
+    if (lane == 0) bulk_wait_all();
+    __syncwarp();
 }
 
 // drop empty results: in-place stream compaction of each query's output
@@ -1124,6 +1245,10 @@ rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool
         p->last_ms = p->last_lean_ms = p->last_heavy_ms = 0;
     }
     clear_stale_error();
+    if (h.status & 4u) {
+        arena_unref(a);
+        return set_err(RB_ETIMEOUT, "batch: a bulk-copy wait ran out of its iteration limit");
+    }
     if (h.status & 3u) {
         *overflow = true;
         p->words_cap = std::max<uint64_t>(p->words_cap, h.words_used);
