@@ -243,6 +243,25 @@ rb_status rb_server_stats(rb_server_t *s, uint64_t *completed, uint64_t *batches
                           uint64_t *peak_inflight);
 void rb_server_destroy(rb_server_t *s);
 
+/* ------------------------------------------------------ allocation-free */
+
+/* rb_to_u32 for callers that cannot allocate device memory: code whose
+ * device memory is wholly reserved by another allocator, or paths that must
+ * never allocate or free (real-time loops, callbacks that must not block).
+ * The paper has no counterpart.  Writes the set's values in ascending order
+ * to dst (DEVICE memory owned by the caller, cap values at most) and *n_out
+ * (may be NULL) gets the cardinality.  It allocates nothing: the decode's
+ * per-container offsets live in a fixed device array of 16384 entries
+ * (128 KB, one per device that loads the library, kept until the process
+ * exits), so a bitmap with more than 16384 containers returns RB_ERANGE, as
+ * does cap below the cardinality.  Every call on a device shares that array:
+ * calls whose work overlaps on the device race.  The first call on each
+ * device looks up the array's device address (set-up, with that device
+ * current); make that first call before any stream capture.  The call only
+ * enqueues work on `stream`: the values are in dst once the stream reaches
+ * it.  RB_ECUDA if a CUDA call fails. */
+rb_status rb_to_u32_noalloc(const rb_t *b, uint32_t *dst, uint64_t cap, uint64_t *n_out, void *stream);
+
 /* ----------------------------------------------------------------- misc */
 
 /* Message describing the calling thread's last error ("" if none). */

@@ -437,6 +437,20 @@ __global__ void k_gather(const uint64_t *descs, const uint8_t *base, uint32_t n,
 
 }  // namespace
 
+namespace rbi {
+
+// Enqueue the decode of b (b->n > 0) into device memory `out` on stream s,
+// with the per-container output offsets in caller-provided device memory
+// `offs` (at least b->n entries).  No allocation, no synchronisation.
+cudaError_t enqueue_decode(const rb *b, uint64_t *offs, uint32_t *out, cudaStream_t s) {
+    k_scan_cards<<<1, 1024, 0, s>>>(b->descs, b->n, offs);
+    const uint32_t grid = (b->n + 7) / 8, gcap = (uint32_t)sm_count() * 8;
+    k_decode<<<grid < gcap ? grid : gcap, 256, 0, s>>>(b->keys, b->descs, b->base, b->n, offs, out);
+    return cudaGetLastError();
+}
+
+}  // namespace rbi
+
 extern "C" {
 
 const char *rb_last_error(void) { return g_err; }

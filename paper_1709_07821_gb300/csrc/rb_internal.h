@@ -130,6 +130,9 @@ inline void clear_stale_error() { (void)cudaGetLastError(); }
 BmView view_of(const rb *b);
 rb *handle_new();
 
+// decode kernels of rb_to_u32 with caller-provided offsets scratch (b->n > 0)
+cudaError_t enqueue_decode(const rb *b, uint64_t *offs, uint32_t *out, cudaStream_t s);
+
 // shared launch schedule
 rb_schedule current_schedule();
 

@@ -1,0 +1,64 @@
+// rb_noalloc.cu - decode a bitmap into caller-provided device memory without
+// allocating any device memory.
+//
+// Some callers cannot allocate: their device memory is entirely reserved by
+// another allocator (a fixed arena they manage themselves), or they run on a
+// path that must never allocate or free (a real-time loop, a callback that
+// must not block on an allocator).  For them rb_to_u32_noalloc keeps the one
+// piece of scratch the decode needs, the per-container output offsets, in a
+// fixed file-scope device array instead of a fresh allocation.
+#include <mutex>
+
+#include "rb_internal.h"
+
+namespace {
+
+constexpr uint32_t NOALLOC_MAX_CONTAINERS = 16384;   // 128 KB of offsets
+
+// Per-container output offsets of every allocation-free decode.  Each device
+// that loads the library holds one copy until the process exits; every call
+// on that device shares it, so calls whose work overlaps on the device race.
+// The scan kernel writes every entry a call reads, so nothing needs clearing.
+static __device__ __align__(256) unsigned long long g_noalloc_offs[NOALLOC_MAX_CONTAINERS];
+
+constexpr int MAX_DEVICES = 256;
+std::mutex g_mu;
+void *g_offs_addr[MAX_DEVICES];   // device address of g_noalloc_offs, per device
+
+}  // namespace
+
+extern "C" rb_status rb_to_u32_noalloc(const rb_t *b, uint32_t *dst, uint64_t cap, uint64_t *n_out, void *stream) {
+    using namespace rbi;
+    clear_stale_error();
+    if (!b) return set_err(RB_EINVAL, "rb_to_u32_noalloc: NULL handle");
+    if (n_out) *n_out = b->card;
+    if (b->n > NOALLOC_MAX_CONTAINERS)
+        return set_err(RB_ERANGE, "rb_to_u32_noalloc: the bitmap has %u containers; the allocation-free decode "
+                                  "handles at most %u (use rb_to_u32)",
+                       b->n, NOALLOC_MAX_CONTAINERS);
+    if (b->card == 0) return RB_OK;
+    if (!dst) return set_err(RB_EINVAL, "rb_to_u32_noalloc: dst is NULL");
+    if (cap < b->card)
+        return set_err(RB_ERANGE, "rb_to_u32_noalloc: capacity %llu below cardinality %llu", (unsigned long long)cap,
+                       (unsigned long long)b->card);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_err(e, "rb_to_u32_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= MAX_DEVICES) return set_err(RB_ERANGE, "rb_to_u32_noalloc: device %d out of range", dev);
+    void *offs = nullptr;
+    {
+        // set-up, once per device, with that device current: in host code the
+        // array's name is only a stand-in, so kernels get its device address
+        std::lock_guard<std::mutex> g(g_mu);
+        if (!g_offs_addr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_offs);
+            if (e != cudaSuccess) return cuda_err(e, "rb_to_u32_noalloc: cudaGetSymbolAddress");
+            g_offs_addr[dev] = p;
+        }
+        offs = g_offs_addr[dev];
+    }
+    e = enqueue_decode(b, reinterpret_cast<uint64_t *>(offs), dst, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_err(e, "rb_to_u32_noalloc: launch");
+    return RB_OK;
+}
