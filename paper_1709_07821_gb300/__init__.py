@@ -407,9 +407,9 @@ class Server:
     def submit(self, op: int, members, count_only: bool = False) -> int:
         r = Request()
         r.op = op
-        r.k = len(members)
+        r.k = len(members)          # more than SERVE_MAX_K is refused by the library
         r.count_only = 1 if count_only else 0
-        for i, m in enumerate(members):
+        for i, m in enumerate(members[:SERVE_MAX_K]):
             r.members[i] = int(m)
         t = ctypes.c_uint64()
         _check(lib().rb_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))

@@ -1,0 +1,123 @@
+"""Serving loop: continuous batching over a device-resident index.  Each
+request's result inside a concurrent, mixed stream must be identical to the
+same query run alone and to the oracle's sequential fold (integer sets:
+tolerance zero)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(oracle_mod, workloads_mod):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1709_07821_gb300 as rb
+    rb.build()
+    W = workloads_mod
+    spec = W.scaled(W.SPECS["serving"], n_bitmaps=48, log10_hi=5.3)
+    pool = W.make_pool(spec)
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    O = [oracle_mod.Bitmap.from_sorted(v) for v in vals]
+    return rb, oracle_mod, W, pool, G, O
+
+
+def test_results_alone_equal_results_in_the_mix(env):
+    rb, orc, W, pool, G, O = env
+    ops, ks, co, mem = W.multi_queries(51, 120, pool.n)
+    srv = rb.Server(G, mem_budget=8 << 30, max_inflight_batches=4, max_batch=16)
+    try:
+        tickets = [srv.submit(int(ops[q]), mem[q, :ks[q]].tolist(), bool(co[q])) for q in range(len(ops))]
+        lat = []
+        for q, t in enumerate(tickets):
+            got, card, latency = srv.wait(t, timeout_ms=60000)
+            members = mem[q, :ks[q]].tolist()
+            alone, card_alone = rb.multi_op(int(ops[q]), [G[m] for m in members], count_only=bool(co[q]))
+            exp = orc.Bitmap.multi(int(ops[q]), [O[m] for m in members])
+            assert card == card_alone == exp.card, q
+            if co[q]:
+                assert got is None
+            else:
+                lay = got.layout()
+                ref = alone.layout()
+                for k in ("keys", "types", "cards", "offs", "payload"):
+                    assert np.array_equal(lay[k], ref[k]), (q, k)
+                    assert np.array_equal(lay[k], exp.layout()[k]), (q, k)
+                got.free()
+                alone.free()
+            assert latency > 0
+            lat.append(latency)
+        st = srv.stats()
+        assert st["completed"] == len(ops)
+        assert st["batches"] >= 1
+    finally:
+        srv.close()
+
+
+def test_requests_arriving_while_batches_run_are_admitted(env):
+    rb, orc, W, pool, G, O = env
+    ops, ks, co, mem = W.multi_queries(52, 200, pool.n)
+    srv = rb.Server(G, mem_budget=8 << 30, max_inflight_batches=3, max_batch=8)
+    results = {}
+    try:
+        def submitter():
+            for q in range(len(ops)):
+                results[q] = srv.submit(int(ops[q]), mem[q, :ks[q]].tolist(), True)
+                if q % 20 == 0:
+                    time.sleep(0.001)
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        for q in range(len(ops)):
+            _, card, _ = srv.wait(results[q], timeout_ms=60000, want_bitmap=False)
+            assert card == orc.Bitmap.multi(int(ops[q]), [O[m] for m in mem[q, :ks[q]]]).card
+        st = srv.stats()
+        assert st["completed"] == len(ops) and st["batches"] > 1
+    finally:
+        srv.close()
+
+
+def test_admission_by_memory(env):
+    rb, orc, W, pool, G, O = env
+    big = sorted(range(pool.n), key=lambda i: -G[i].card)[:8]
+    # a budget below one request's worst case refuses it outright
+    srv = rb.Server(G, mem_budget=1 << 16, max_inflight_batches=2, max_batch=4)
+    try:
+        with pytest.raises(rb.RoaringError) as ei:
+            srv.submit(rb.OR, big)
+        assert ei.value.status == rb.EBUSY
+        t = srv.submit(rb.OR, big, count_only=True)            # count-only needs no result memory
+        _, card, _ = srv.wait(t)
+        assert card == orc.Bitmap.multi(1, [O[m] for m in big]).card
+    finally:
+        srv.close()
+    # a small budget still serves every request, admitting more as results
+    # are freed
+    srv = rb.Server(G, mem_budget=256 << 20, max_inflight_batches=2, max_batch=4)
+    try:
+        ts = [srv.submit(rb.OR, big[i:i + 3]) for i in range(5)]
+        for i, t in enumerate(ts):
+            bm, card, _ = srv.wait(t, timeout_ms=60000)
+            assert card == orc.Bitmap.multi(1, [O[m] for m in big[i:i + 3]]).card
+            bm.free()
+    finally:
+        srv.close()
+
+
+def test_bad_requests(env):
+    rb, orc, W, pool, G, O = env
+    srv = rb.Server(G, mem_budget=1 << 30)
+    try:
+        with pytest.raises(rb.RoaringError):
+            srv.submit(rb.XOR, [0, 1])                 # multi-way is AND / OR only
+        with pytest.raises(rb.RoaringError):
+            srv.submit(rb.AND, [0, pool.n + 5])        # member out of range
+        with pytest.raises(rb.RoaringError):
+            srv.submit(rb.AND, list(range(9)))         # more than 8 members
+    finally:
+        srv.close()
