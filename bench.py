@@ -118,7 +118,7 @@ class OracleSample:
     runs the materialised op plus the Jaccard counts of each pair on the host
     cores, pairs spread over a thread pool (ctypes releases the GIL)."""
 
-    def __init__(self, pool, ops, a, b, sample_values=3e9, threads=None):
+    def __init__(self, pool, ops, a, b, sample_values=2e10, threads=None):
         import oracle
         oracle.build()
         self.threads = threads or os.cpu_count() or 1
@@ -129,7 +129,7 @@ class OracleSample:
             self.sample.append(i)
             need.update([int(a[i]), int(b[i])])
             est += int(self.sizes[a[i]]) + int(self.sizes[b[i]])
-            if est > sample_values or len(self.sample) >= 4096:
+            if est > sample_values or len(self.sample) >= 16384:
                 break
         need = sorted(need)
         with cf.ThreadPoolExecutor(self.threads) as ex:
@@ -237,21 +237,20 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        outs, counts = plan_m.run()
-        _, inter = plan_j.run()
+        # results stay raw handles; they are released in one call after use
+        outs, counts = plan_m.run(raw=True)
+        _, inter = plan_j.run(want_bitmaps=False)
         return outs, counts, inter
 
     for _ in range(args.warmup):
         outs, _, _ = step()
-        for o in outs:
-            if o is not None:
-                o.free()
+        plan_m.free_raw(outs)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     clocks = Clocks(local) if rank == 0 else None
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kms, alg, outb, step_ms = [], [], [], []
+    kms, jst, alg, outb, step_ms = [], [], [], [], []
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
@@ -259,14 +258,13 @@ def run_ours(args):
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         outs, counts, inter = step()
-        s1.record(stream)
         st = plan_m.stats()
         kms.append(st)
+        jst.append(plan_j.stats())
         alg.append(st["alg_bytes"])
         outb.append(st["out_bytes"])
-        for o in outs:
-            if o is not None:
-                o.free()
+        plan_m.free_raw(outs)
+        s1.record(stream)
         s1.synchronize()
         step_ms.append(s0.elapsed_time(s1))
     ev1.record(stream)
@@ -322,10 +320,14 @@ def run_ours(args):
                 "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
                 "pair_stage": {"lean_ms": lean_ms, "heavy_ms": heavy_ms, "lean_bytes": lean_b,
                                "heavy_bytes": heavy_b, "achieved_gbs": stage_gbs, "frac": stage_gbs / peak,
-                               "deferred_pairs": statistics.mean(s["deferred"] for s in kms)}}
+                               "deferred_pairs": statistics.mean(s["deferred"] for s in kms)},
+                "jaccard_stage": {"lean_ms": statistics.mean(s["lean_ms"] for s in jst),
+                                  "heavy_ms": statistics.mean(s["heavy_ms"] for s in jst),
+                                  "alg_bytes": statistics.mean(s["lean_bytes"] + s["heavy_bytes"] for s in jst)}}
 
     # per-pair baseline on the same GPU: rb_apply one pair at a time
     per = per_pair_leg(rb, G, ops, a, b, sizes, n=args.per_pair_sample)
+    serving = None if args.no_serving else serving_leg(rb, G, sizes)
     cpu = cpu_oracle_leg(pool, ops, a, b, budget_s=args.cpu_budget) if not args.no_cpu else None
 
     line = {"metric": "batched Roaring AND/OR Gints/s", "value": value, "unit": "Gints/s", "n_gpus": ws,
@@ -342,7 +344,7 @@ def run_ours(args):
             "gpu_launches": 5 * args.steps,
             "clocks": clk,
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
-            "per_pair": per, "bitset_and_or": bitset_legs}
+            "per_pair": per, "bitset_and_or": bitset_legs, "serving": serving}
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -403,6 +405,56 @@ def bitset_subset_legs(rb, G, pool, sizes, n_pairs=16384, reps=5):
     return out
 
 
+def serving_leg(rb, G, sizes, rates=(1e3, 1e4, 1e5, 1e6), seconds=2.0, max_queries=20000):
+    """Open-loop Poisson load on the serving loop with the pool as its
+    resident index: multi-way AND/OR of 2..8 members, materialised or
+    count-only (50/50).  Latency is submit -> completion on the device, as
+    the library measures it; results are freed as they arrive."""
+    import queue
+    import threading
+    import workloads as W
+    out = []
+    srv = rb.Server(G, mem_budget=64 << 30, max_inflight_batches=4, max_batch=256)
+    try:
+        for rate in rates:
+            n = int(min(max_queries, max(200, rate * seconds)))
+            ops, ks, co, mem = W.multi_queries(5, n, len(G))
+            arrivals = W.poisson_arrivals(5, n, rate)
+            q = queue.Queue()
+            lat = []
+            done_units = [0.0]
+
+            def waiter():
+                for _ in range(n):
+                    t, units = q.get()
+                    bm, card, l = srv.wait(t, timeout_ms=600000)
+                    if bm is not None:
+                        bm.free()
+                    lat.append(l)
+                    done_units[0] += units
+            th = threading.Thread(target=waiter)
+            th.start()
+            t0 = time.perf_counter()
+            for i in range(n):
+                now = time.perf_counter() - t0
+                if arrivals[i] > now:
+                    time.sleep(arrivals[i] - now)
+                members = mem[i, :ks[i]]
+                tk = srv.submit(int(ops[i]), members.tolist(), bool(co[i]))
+                q.put((tk, float(sizes[members].sum())))
+            submit_s = time.perf_counter() - t0
+            th.join()
+            wall = time.perf_counter() - t0
+            out.append({"offered_qps": rate, "achieved_offered_qps": n / submit_s, "queries": n,
+                        "throughput_qps": n / wall, "gints_s": done_units[0] / wall / 1e9,
+                        "p50_ms": float(np.percentile(lat, 50)) * 1e3, "p99_ms": float(np.percentile(lat, 99)) * 1e3})
+        st = srv.stats()
+    finally:
+        srv.close()
+    return {"loads": out, "batches": st["batches"], "peak_inflight": st["peak_inflight"],
+            "index": f"the {len(G)}-bitmap pool resident on the device", "budget_bytes": 64 << 30}
+
+
 def per_pair_leg(rb, G, ops, a, b, sizes, n=512):
     """The same pairs through rb_apply + rb_jaccard one pair at a time."""
     import torch
@@ -435,6 +487,7 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-subsets", action="store_true", help="skip the bitset-dominated AND/OR legs")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--ref-budget", type=float, default=5.0, help="seconds of oracle work per reference step")
     ap.add_argument("--per-pair-sample", type=int, default=512)

@@ -99,6 +99,10 @@ rb_status rb_export_layout(const rb_t *b, uint16_t *keys, uint8_t *types, uint32
  * handles of the same batch is returned when its last handle is freed. */
 void rb_free(rb_t *b);
 
+/* rb_free on each of hs[0..n) (NULL entries are ignored), e.g. all results
+ * of a batch at once. */
+void rb_free_array(rb_t *const *hs, uint64_t n);
+
 /* ------------------------------------------------------------- pairwise */
 
 /* out = a op b as a new canonical bitmap (Sec. 1 set operations; Sec. 5
@@ -176,15 +180,18 @@ void rb_plan_free(rb_plan_t *p);
 
 /* Launch schedule of the container-pair kernels: the heavy kernel's warps
  * per CTA (2, 4 or 8; each warp owns 16 KB of shared tiles) and CTAs per SM;
- * the largest container pair, in intervals (array values or runs on both
- * sides), that one lane of the lean kernel sweeps alone (bigger pairs and all
- * bitsets are deferred to the heavy kernel); and the lean kernel's CTAs of
- * 256 threads per SM (0 = 4). */
+ * the largest array pair (values on both sides) that one lane of the lean
+ * kernel merges alone (larger array pairs up to 1024 values are merged by the
+ * whole warp; bitsets and larger containers are deferred to the heavy
+ * kernel); the lean kernel's CTAs of 128 threads per SM (0 = 8); and how many
+ * 128-byte lines of each queued container's payload the lean kernel hints
+ * into L2 ahead of use (0 = none). */
 typedef struct {
     uint32_t warps_per_cta;
     uint32_t ctas_per_sm;
     uint32_t small_intervals;
     uint32_t lean_ctas_per_sm;
+    uint32_t prefetch_lines;
 } rb_schedule;
 rb_status rb_set_schedule(const rb_schedule *s);
 rb_status rb_get_schedule(rb_schedule *s);

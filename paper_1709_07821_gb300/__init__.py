@@ -37,11 +37,13 @@ class Query(ctypes.Structure):
 
 class Schedule(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("small_intervals", ctypes.c_uint32), ("lean_ctas_per_sm", ctypes.c_uint32)]
+                ("small_intervals", ctypes.c_uint32), ("lean_ctas_per_sm", ctypes.c_uint32),
+                ("prefetch_lines", ctypes.c_uint32)]
 
     def as_dict(self):
         return {"warps_per_cta": self.warps_per_cta, "ctas_per_sm": self.ctas_per_sm,
-                "small_intervals": self.small_intervals, "lean_ctas_per_sm": self.lean_ctas_per_sm}
+                "small_intervals": self.small_intervals, "lean_ctas_per_sm": self.lean_ctas_per_sm,
+                "prefetch_lines": self.prefetch_lines}
 
 
 class PlanTiming(ctypes.Structure):
@@ -104,6 +106,8 @@ def _sig(L):
     for name in ("rb_free", "rb_plan_free", "rb_server_destroy"):
         getattr(L, name).argtypes = [vp]
         getattr(L, name).restype = None
+    L.rb_free_array.argtypes = [vp, u64]
+    L.rb_free_array.restype = None
     L.rb_last_error.restype = ctypes.c_char_p
     L.rb_version.restype = ctypes.c_char_p
 
@@ -337,17 +341,23 @@ class Plan:
                                     ctypes.byref(h)))
         self._h = h.value
 
-    def run(self, stream=None, want_bitmaps=True):
+    def run(self, stream=None, want_bitmaps=True, raw=False):
+        """Run the batch.  Returns (bitmaps, counts); with raw=True the results
+        stay a ctypes array of handles (release it with free_raw), and with
+        want_bitmaps=False they are released at once."""
         outs = (ctypes.c_void_p * max(1, self.n))()
         counts = np.zeros(self.n, np.uint64)
         _check(lib().rb_plan_run(self._h, outs, counts.ctypes.data if self.n else None, _stream(stream)))
-        bms = [Bitmap(outs[i]) if outs[i] else None for i in range(self.n)]
+        if raw:
+            return outs, counts
         if not want_bitmaps:
-            for x in bms:
-                if x is not None:
-                    x.free()
-            bms = None
-        return bms, counts
+            lib().rb_free_array(outs, self.n)
+            return None, counts
+        return [Bitmap(outs[i]) if outs[i] else None for i in range(self.n)], counts
+
+    def free_raw(self, outs):
+        """Release the handles of a raw run."""
+        lib().rb_free_array(outs, self.n)
 
     def stats(self):
         t = PlanTiming()
@@ -380,8 +390,9 @@ def get_schedule() -> dict:
     return s.as_dict()
 
 
-def set_schedule(warps_per_cta: int, ctas_per_sm: int, small_intervals: int, lean_ctas_per_sm: int = 0):
-    s = Schedule(warps_per_cta, ctas_per_sm, small_intervals, lean_ctas_per_sm)
+def set_schedule(warps_per_cta: int, ctas_per_sm: int, small_intervals: int, lean_ctas_per_sm: int = 0,
+                 prefetch_lines: int = 4):
+    s = Schedule(warps_per_cta, ctas_per_sm, small_intervals, lean_ctas_per_sm, prefetch_lines)
     _check(lib().rb_set_schedule(ctypes.byref(s)))
 
 

@@ -19,7 +19,7 @@ std::mutex g_alloc_mu;
 rb_alloc_fn g_alloc = nullptr;
 rb_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
-rb_schedule g_sched = {4, 3, 64, 0};
+rb_schedule g_sched = {4, 3, 64, 0, 4};
 std::mutex g_sched_mu;
 }  // namespace
 
@@ -475,6 +475,7 @@ rb_status rb_set_schedule(const rb_schedule *s) {
         return set_err(RB_EINVAL, "ctas_per_sm out of range for 16 KB of tiles per warp");
     if (s->small_intervals > 2047) return set_err(RB_EINVAL, "small_intervals must be <= 2047");
     if (s->lean_ctas_per_sm > 8) return set_err(RB_EINVAL, "lean_ctas_per_sm must be <= 8");
+    if (s->prefetch_lines > 64) return set_err(RB_EINVAL, "prefetch_lines must be <= 64");
     std::lock_guard<std::mutex> g(g_sched_mu);
     g_sched = *s;
     return RB_OK;
@@ -490,6 +491,11 @@ void rb_free(rb_t *b) {
     if (!b) return;
     arena_unref(b->arena);
     delete b;
+}
+
+void rb_free_array(rb_t *const *hs, uint64_t n) {
+    if (!hs) return;
+    for (uint64_t i = 0; i < n; i++) rb_free(hs[i]);
 }
 
 rb_status rb_cardinality(const rb_t *b, uint64_t *out) {

@@ -80,6 +80,8 @@ struct PairParams {
     unsigned long long n_tiles;
     uint32_t n_pairs;
     uint32_t small_iv;
+    uint32_t prefetch;   // payload lines hinted into L2 per queued container
+    uint32_t pad;
 };
 
 // ------------------------------------------------------------ allocation
@@ -293,6 +295,12 @@ __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *
 
 // ------------------------------------------------------------ lean kernel
 
+// hint the first `lines` 128-byte lines of a payload into L2
+__device__ __forceinline__ void prefetch_payload(const uint8_t *p, uint32_t bytes, uint32_t lines) {
+    const uint32_t n = min((bytes + 127) / 128, lines);
+    for (uint32_t i = 0; i < n; i++) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 128 * i));
+}
+
 enum : uint32_t { M_NONE = 0, M_LANE_ARR, M_LANE_SWEEP, M_LANE_COPY, M_WARP_ARR, M_WARP_COPY, M_DEFER };
 constexpr uint32_t WARP_MERGE_MAX = 1024;   // values of both arrays the warp merges through shared memory
 constexpr uint32_t RUN_SWEEP_MAX = 512;     // intervals one lane sweeps when runs are involved
@@ -453,6 +461,13 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t
         es->keys[pd.pos_base + pos] = (uint16_t)key;
     }
     const bool act = mode != M_NONE && mode != M_DEFER;
+    if (act && P.prefetch) {
+        // start fetching the payloads into L2 now; the queue is processed
+        // after one or two more tiles have been resolved
+        const uint64_t d1 = kind == K_COPY_B ? db : da;
+        prefetch_payload((kind == K_COPY_B ? B.base : A.base) + d_off(d1), in_payload_bytes(d1), P.prefetch);
+        if (kind == K_PAIR) prefetch_payload(B.base + d_off(db), in_payload_bytes(db), P.prefetch);
+    }
     const uint32_t am = __ballot_sync(FULL, act);
     if (act) {
         Item it;
@@ -580,7 +595,12 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
             bytes = word_alloc_bytes(ca.type, ca.card, ca.runs);
         }
     }
-    const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
+    // one allocation for the batch; copies come first, in item order, so that
+    // consecutive copies of consecutive containers stay contiguous
+    const bool is_copy = mode == M_LANE_COPY || mode == M_WARP_COPY;
+    const uint32_t cbytes = is_copy ? bytes : 0, obytes = is_copy ? 0 : bytes;
+    const uint32_t cincl = warp_incl(cbytes, lane), ctotal = __shfl_sync(FULL, cincl, 31);
+    const uint32_t oincl = warp_incl(obytes, lane), total = ctotal + __shfl_sync(FULL, oincl, 31);
     unsigned long long wbase = 0;
     bool ok = true;
     if (total) {
@@ -589,7 +609,8 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
         ok = wbase + total <= es->words_cap;
         if (!ok && lane == 0) atomicOr(&es->status, 1u);
     }
-    const uint64_t off = (ok && bytes) ? es->words_off + wbase + incl - bytes : ALLOC_FAIL;
+    const uint64_t off = (ok && bytes) ? es->words_off + wbase + (is_copy ? cincl - cbytes : ctotal + oincl - obytes)
+                                       : ALLOC_FAIL;
 
     uint64_t desc = DESC_EMPTY;
     uint32_t card = 0;
@@ -622,15 +643,45 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
             desc = mk_desc(lc, lt, lt == T_RUN ? lr : 0, off);
             card = lc;
         }
-    } else if (mode == M_LANE_COPY && off != ALLOC_FAIL) {
-        const uint32_t *S = reinterpret_cast<const uint32_t *>(ca.p);
-        uint32_t *D = reinterpret_cast<uint32_t *>(es->arena + off);
-        for (uint32_t x = 0; x < bytes / 4; x++) D[x] = __ldg(S + x);
+    } else if (is_copy && off != ALLOC_FAIL) {
         desc = mk_desc(ca.card, ca.type, ca.type == T_RUN ? ca.runs : 0, off);
         card = ca.card;
     }
-    // warp-sized items, one at a time
-    uint32_t wq = __ballot_sync(FULL, mode == M_WARP_ARR || mode == M_WARP_COPY);
+    // copies of array and run containers, by the whole warp: one coalesced
+    // memcpy when every copied container follows the previous one in both
+    // source and destination, else item by item in 32-word chunks
+    const uint32_t cm = __ballot_sync(FULL, is_copy && off != ALLOC_FAIL);
+    if (cm) {
+        const uint32_t nw = (is_copy && off != ALLOC_FAIL) ? bytes / 4 : 0;
+        const unsigned long long src = (unsigned long long)ca.p;
+        const unsigned long long dst = (unsigned long long)(es->arena + off);
+        const uint32_t below = cm & lanemask_lt(lane);
+        const int prev = below ? 31 - __clz(below) : -1;
+        const unsigned long long psrc = __shfl_sync(FULL, src, prev < 0 ? lane : prev);
+        const unsigned long long pdst = __shfl_sync(FULL, dst, prev < 0 ? lane : prev);
+        const uint32_t pnw = __shfl_sync(FULL, nw, prev < 0 ? lane : prev);
+        const bool follows = !((cm >> lane) & 1u) || prev < 0 || (src == psrc + 4ull * pnw && dst == pdst + 4ull * pnw);
+        const int first = __ffs(cm) - 1;
+        if (__all_sync(FULL, follows)) {
+            const uint32_t *S = reinterpret_cast<const uint32_t *>(__shfl_sync(FULL, src, first));
+            uint32_t *D = reinterpret_cast<uint32_t *>(__shfl_sync(FULL, dst, first));
+            const uint32_t T = warp_sum(nw);
+#pragma unroll 4
+            for (uint32_t g = lane; g < T; g += 32) D[g] = __ldg(S + g);
+        } else {
+            uint32_t q = cm;
+            while (q) {
+                const int k = __ffs(q) - 1;
+                q &= q - 1;
+                const uint32_t *S = reinterpret_cast<const uint32_t *>(__shfl_sync(FULL, src, k));
+                uint32_t *D = reinterpret_cast<uint32_t *>(__shfl_sync(FULL, dst, k));
+                const uint32_t n = __shfl_sync(FULL, nw, k);
+                for (uint32_t g = lane; g < n; g += 32) D[g] = __ldg(S + g);
+            }
+        }
+    }
+    // warp-sized array merges, one at a time
+    uint32_t wq = __ballot_sync(FULL, mode == M_WARP_ARR);
     while (wq) {
         const int src = __ffs(wq) - 1;
         wq &= wq - 1;
@@ -639,26 +690,13 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
         const unsigned long long pa_s = __shfl_sync(FULL, (unsigned long long)ca.p, src);
         const unsigned long long pb_s = __shfl_sync(FULL, (unsigned long long)cb.p, src);
         const uint32_t na_s = __shfl_sync(FULL, ca.card, src), nb_s = __shfl_sync(FULL, cb.card, src);
-        const uint32_t by_s = __shfl_sync(FULL, bytes, src);
-        uint64_t dsc = DESC_EMPTY;
         uint32_t c = 0;
-        if (m_s == M_WARP_ARR) {
-            dsc = warp_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s), na_s,
-                                    reinterpret_cast<const uint16_t *>(pb_s), nb_s, stg, lane, off_s, c);
-        } else if (off_s != ALLOC_FAIL) {
-            const uint32_t *S = reinterpret_cast<const uint32_t *>(pa_s);
-            uint32_t *D = reinterpret_cast<uint32_t *>(es->arena + off_s);
-            for (uint32_t x = lane; x < by_s / 4; x += 32) D[x] = __ldg(S + x);
-            __syncwarp();
-        }
+        const uint64_t dsc = warp_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s), na_s,
+                                               reinterpret_cast<const uint16_t *>(pb_s), nb_s, stg, lane, off_s, c);
+        (void)m_s;
         if (lane == (uint32_t)src) {
-            if (m_s == M_WARP_ARR) {
-                desc = dsc;
-                card = c;
-            } else if (off_s != ALLOC_FAIL) {
-                desc = mk_desc(ca.card, ca.type, ca.type == T_RUN ? ca.runs : 0, off_s);
-                card = ca.card;
-            }
+            desc = dsc;
+            card = c;
         }
     }
     // results, and per-query sums over the lanes of the same query
@@ -674,7 +712,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
         if (wsum) atomicAdd(&P.stats[it.p].words, (unsigned long long)wsum);
     }
     if (has) {
-        bytes_acc += (mode == M_LANE_COPY || mode == M_WARP_COPY) ? in_payload_bytes(dx)
+        bytes_acc += is_copy ? in_payload_bytes(dx)
                                                                   : in_payload_bytes(it.da) + in_payload_bytes(it.db);
         if (desc != DESC_EMPTY) bytes_acc += payload_bytes(d_type(desc), d_card(desc), d_runs(desc)) + 10;
     }
@@ -966,7 +1004,7 @@ struct rb_plan {
     cudaStream_t ps = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev_in = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    rb_schedule gsched = {0, 0, 0, 0};
+    rb_schedule gsched = {0, 0, 0, 0, 0};
     double last_ms = 0, last_lean_ms = 0, last_heavy_ms = 0;
     uint64_t last_alg = 0, last_out = 0, last_lean_bytes = 0, last_heavy_bytes = 0, last_deferred = 0;
     cudaStream_t alloc_stream = nullptr;
@@ -1136,6 +1174,8 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     P.n_tiles = p->total_tiles;
     P.n_pairs = (uint32_t)nq;
     P.small_iv = sc.small_intervals;
+    P.prefetch = sc.prefetch_lines;
+    P.pad = 0;
     init_kernel_attrs();
     if ((e = cudaEventRecordWithFlags(p->ev0, s, evf)) != cudaSuccess) return e;
     if (p->total_tiles) {
@@ -1461,7 +1501,7 @@ rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *be
     for (auto &sh : heavy) {
         for (uint32_t sm : smalls) {
             for (uint32_t ln : leans) {
-                rb_schedule c = {sh[0], sh[1], sm, ln};
+                rb_schedule c = {sh[0], sh[1], sm, ln, saved.prefetch_lines};
                 if (rb_set_schedule(&c) != RB_OK) continue;
                 double tot = 0;
                 bool ok = true;
