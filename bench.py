@@ -55,6 +55,39 @@ def dist_env():
     return ws, rank, local
 
 
+def _reduce(value, op):
+    """value reduced over the ranks of the default process group (as is
+    when there is none); tensors live on the backend's device."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    dist.barrier()
+    return float(t.item())
+
+
+def reduce_max(value):
+    """Slowest rank's value: the whole job ends when its last replica does."""
+    import torch.distributed as dist
+    return _reduce(value, dist.ReduceOp.MAX)
+
+
+def reduce_sum(value):
+    """Sum over ranks: replicas draw different seeded workloads, so the
+    job's units are the sum of every rank's units."""
+    import torch.distributed as dist
+    return _reduce(value, dist.ReduceOp.SUM)
+
+
+def job_value(units_total, max_ms_per_step):
+    """Whole-job Gints/s: all ranks' input values per step over the slowest
+    rank's step time."""
+    return units_total / (max_ms_per_step / 1e3) / 1e9
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -271,13 +304,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     total_ms = ev0.elapsed_time(ev1)
     clk = clocks.stop() if clocks else None
-    t = torch.tensor([total_ms], device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-    total_ms = float(t.item())
+    total_ms = reduce_max(total_ms)
     ms_per_step = total_ms / args.steps
-    value = units * ws / (ms_per_step / 1e3) / 1e9
+    units_total = reduce_sum(units)
+    value = job_value(units_total, ms_per_step)
 
     # end to end through the public API: queries from host memory, counts back
     # to host, one rb_batch_op + rb_batch_jaccard per step (no plan reuse)
@@ -290,12 +320,12 @@ def run_ours(args):
             if o is not None:
                 o.free()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t1) / e2e_steps
+    e2e_s = reduce_max((time.perf_counter() - t1) / e2e_steps)
 
     bitset_legs = {} if args.no_subsets else bitset_subset_legs(rb, G, pool, sizes)
     h2d = 2 * (32 * len(G) + 32 * n_pairs + 8 * (n_pairs + 1) + 128) + 2 * 16 * n_pairs
     d2h = 2 * (40 * n_pairs + 128) + 8 * n_pairs * 4
-    e2e = {"value": units / e2e_s / 1e9, "unit": "Gints/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+    e2e = {"value": units_total / e2e_s / 1e9, "unit": "Gints/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "what": "rb_batch_op + rb_batch_jaccard from host query arrays, counts/Jaccard to host; "
                    "index resident on the device"}
 
@@ -336,7 +366,7 @@ def run_ours(args):
             "config": {"workload": "batched: 4096-bitmap pool over [0,2^32), c log-uniform 10..1e7, 40/30/30 "
                                    "sparse/dense/runs; 65,536 pairs AND/OR/ANDNOT/XOR 40/30/15/15 materialised "
                                    "+ Jaccard count batch", "global_batch": n_pairs * ws,
-                       "pool_bytes": pool_bytes, "units_per_step": units,
+                       "pool_bytes": pool_bytes, "units_per_step": units_total,
                        "l2": "inputs larger than L2 (pool and outputs are GBs), no flush",
                        "parallelism": f"replicas x{ws}", "schedule": rb.get_schedule()},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

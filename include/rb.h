@@ -271,6 +271,18 @@ rb_status rb_to_u32_noalloc(const rb_t *b, uint32_t *dst, uint64_t cap, uint64_t
 
 /* ----------------------------------------------------------------- misc */
 
+/* Self-test of the bounded-wait error path; the paper has no counterpart.
+ * Every spin-wait in the library's kernels (the bulk-copy barriers of the
+ * heavy kernel) gives up after a cycle limit, records the timeout in a
+ * status word and returns, so that the host reports RB_ETIMEOUT and the
+ * context stays usable.  This call runs one warp that waits on a
+ * shared-memory barrier expecting two arrivals, with limit_cycles (1..2^31
+ * SM cycles) as the limit: with complete != 0 both arrivals happen and it
+ * returns RB_OK; with complete == 0 only one does, the wait runs out and it
+ * returns RB_ETIMEOUT.  Synchronises `stream`.  RB_EINVAL for a limit out of
+ * range, RB_ENOMEM / RB_ECUDA as elsewhere. */
+rb_status rb_selftest_wait(uint64_t limit_cycles, int complete, void *stream);
+
 /* Message describing the calling thread's last error ("" if none). */
 const char *rb_last_error(void);
 

@@ -98,6 +98,7 @@ def _sig(L):
         "rb_server_submit": [vp, ctypes.POINTER(Request), pu64],
         "rb_server_wait": [vp, u64, i32, pvp, pu64, pdbl],
         "rb_server_stats": [vp, pu64, pu64, pu64],
+        "rb_selftest_wait": [u64, ctypes.c_int, vp],
     }
     for name, args in spec.items():
         f = getattr(L, name)
@@ -394,6 +395,47 @@ def set_schedule(warps_per_cta: int, ctas_per_sm: int, small_intervals: int, lea
                  prefetch_lines: int = 4):
     s = Schedule(warps_per_cta, ctas_per_sm, small_intervals, lean_ctas_per_sm, prefetch_lines)
     _check(lib().rb_set_schedule(ctypes.byref(s)))
+
+
+def selftest_wait(limit_cycles: int, complete: bool, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the rb_status code (OK or
+    ETIMEOUT) rather than raising."""
+    return lib().rb_selftest_wait(int(limit_cycles), 1 if complete else 0, _stream(stream))
+
+
+class allocator:
+    """Context manager that routes the library's device allocations through
+    alloc(nbytes, stream) -> int pointer or None and release(ptr, nbytes,
+    stream), then restores PyTorch's caching allocator."""
+
+    def __init__(self, alloc, release):
+        L = lib()
+
+        @ALLOC_FN
+        def _a(nbytes, stream, ctx):
+            try:
+                return alloc(int(nbytes), int(stream or 0))
+            except Exception:
+                return None
+
+        @FREE_FN
+        def _f(ptr, nbytes, stream, ctx):
+            try:
+                release(int(ptr), int(nbytes), int(stream or 0))
+            except Exception:
+                pass
+
+        self._fns = (_a, _f)
+        self._L = L
+
+    def __enter__(self):
+        _keep.extend(self._fns)
+        _check(self._L.rb_set_allocator(self._fns[0], self._fns[1], None))
+        return self
+
+    def __exit__(self, *exc):
+        _install_torch_allocator(self._L)
+        return False
 
 
 def multi_op(op: int, inputs, count_only: bool = False, stream=None):

@@ -65,11 +65,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // after about one second of SM clock (2^31 cycles) and returns false (the
 // caller records the error and stops using the tiles)
 constexpr long long MBAR_WAIT_CYCLES = 1ll << 31;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > MBAR_WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, MBAR_WAIT_CYCLES);
 }
 
 __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
@@ -102,6 +105,7 @@ __device__ __forceinline__ uint32_t warp_xor_incl(uint32_t x, uint32_t lane) {
 // first index i in sorted keys[0..n) with keys[i] >= key
 __device__ __forceinline__ uint32_t lower_bound16(const uint16_t *keys, uint32_t n, uint32_t key) {
     uint32_t lo = 0, hi = n;
+#pragma unroll 1
     while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;
         if ((uint32_t)__ldg(keys + mid) < key) lo = mid + 1;
@@ -141,6 +145,21 @@ __device__ __forceinline__ uint64_t apply_op(uint32_t op, uint64_t a, uint64_t b
         case OP_ANDNOT: return a & ~b;
         default: return a ^ b;
     }
+}
+// the op as a truth table over (in a, in b): masks m11, m10, m01 are all ones
+// when the result holds a value present in both, only in a, only in b
+struct OpMasks {
+    uint64_t m11, m10, m01;
+};
+__device__ __forceinline__ OpMasks op_masks(uint32_t op) {
+    OpMasks m;
+    m.m11 = (op == OP_AND || op == OP_OR) ? ~0ull : 0ull;
+    m.m10 = (op != OP_AND) ? ~0ull : 0ull;
+    m.m01 = (op == OP_OR || op == OP_XOR) ? ~0ull : 0ull;
+    return m;
+}
+__device__ __forceinline__ uint64_t apply_masks(const OpMasks &m, uint64_t a, uint64_t b) {
+    return (a & b & m.m11) | (a & ~b & m.m10) | (~a & b & m.m01);
 }
 __device__ __forceinline__ bool member(uint32_t op, bool ina, bool inb) {
     switch (op) {
@@ -192,7 +211,7 @@ __device__ __forceinline__ uint64_t pxor64(uint64_t x) {
 
 // expand a run container: toggle bit s and bit e+1 of every run [s, e], then
 // a prefix XOR over the 65536-bit string turns the toggles into the runs
-__device__ inline void t_from_runs(uint64_t *T, const uint32_t *runs, uint32_t r, uint32_t lane) {
+static __device__ __noinline__ void t_from_runs(uint64_t *T, const uint32_t *runs, uint32_t r, uint32_t lane) {
     t_zero(T, lane);
     __syncwarp();
     uint32_t *T32 = reinterpret_cast<uint32_t *>(T);
@@ -226,7 +245,7 @@ __device__ inline void t_from_runs(uint64_t *T, const uint32_t *runs, uint32_t r
     __syncwarp();
 }
 
-__device__ __forceinline__ void t_decode(uint64_t *T, const CRef &c, uint32_t lane) {
+static __device__ __noinline__ void t_decode(uint64_t *T, const CRef &c, uint32_t lane) {
     if (c.type == T_BITSET) {
         t_load_bitset(T, reinterpret_cast<const uint64_t *>(c.p), lane);
     } else if (c.type == T_ARRAY) {
@@ -249,10 +268,11 @@ __device__ __forceinline__ void t_combine(uint64_t *dst, const uint64_t *a, cons
     const ulonglong2 *B2 = reinterpret_cast<const ulonglong2 *>(b);
     ulonglong2 *D2 = reinterpret_cast<ulonglong2 *>(dst);
     uint32_t cc = 0, rr = 0, carry = 0;
+    const OpMasks M = op_masks(op);
 #pragma unroll 4
     for (int k = 0; k < 16; k++) {
         ulonglong2 x = A2[32 * k + lane], y = B2[32 * k + lane];
-        uint64_t z0 = apply_op(op, x.x, y.x), z1 = apply_op(op, x.y, y.y);
+        uint64_t z0 = apply_masks(M, x.x, y.x), z1 = apply_masks(M, x.y, y.y);
         if (STORE) D2[32 * k + lane] = make_ulonglong2(z0, z1);
         cc += __popcll(z0) + __popcll(z1);
         uint32_t top = (uint32_t)(z1 >> 63);
@@ -268,7 +288,7 @@ __device__ __forceinline__ void t_combine(uint64_t *dst, const uint64_t *a, cons
 // array container from a tile (Sec. 3.1: extract the positions of the set
 // bits word by word; here each lane extracts its words and a warp scan of
 // the per-lane counts places them)
-__device__ inline void t_emit_array(const uint64_t *T, uint16_t *out, uint32_t lane) {
+static __device__ __noinline__ void t_emit_array(const uint64_t *T, uint16_t *out, uint32_t lane) {
     const ulonglong2 *T2 = reinterpret_cast<const ulonglong2 *>(T);
     uint32_t base = 0;
     for (int k = 0; k < 16; k++) {
@@ -294,7 +314,7 @@ __device__ inline void t_emit_array(const uint64_t *T, uint16_t *out, uint32_t l
 // run container from a tile: run starts (set bit, clear predecessor) go to
 // S, run ends (clear bit after a set one, minus one) to E, both in order;
 // then each run is written as start | (length - 1) << 16
-__device__ inline void t_emit_runs(const uint64_t *T, uint16_t *S, uint16_t *E, uint32_t *out, uint32_t r,
+static __device__ __noinline__ void t_emit_runs(const uint64_t *T, uint16_t *S, uint16_t *E, uint32_t *out, uint32_t r,
                             uint32_t lane) {
     const ulonglong2 *T2 = reinterpret_cast<const ulonglong2 *>(T);
     uint32_t bs = 0, be = 0, carry = 0;
@@ -364,7 +384,7 @@ __device__ __forceinline__ void l_emit_array(const uint16_t *L, uint32_t c, uint
 
 // runs of a sorted list: compact the indexes of run starts into SI, then run
 // k spans L[SI[k]] .. L[SI[k+1] - 1]
-__device__ inline void l_emit_runs(const uint16_t *L, uint32_t c, uint32_t r, uint16_t *SI, uint32_t *out,
+static __device__ __noinline__ void l_emit_runs(const uint16_t *L, uint32_t c, uint32_t r, uint16_t *SI, uint32_t *out,
                             uint32_t lane) {
     uint32_t base = 0;
     for (uint32_t j0 = 0; j0 < c; j0 += 32) {
@@ -414,7 +434,7 @@ __device__ __forceinline__ void iv_at(const IvSrc &s, uint32_t i, uint32_t &lo, 
 // result's cardinality c and runs r; with EMIT it also writes the result as
 // an array (u16 values) or as runs (u32 start | (length - 1) << 16).
 template <bool EMIT>
-__device__ inline void lane_sweep(uint32_t op, const IvSrc &A, const IvSrc &B, uint32_t &c, uint32_t &r,
+__device__ __noinline__ void lane_sweep(uint32_t op, const IvSrc &A, const IvSrc &B, uint32_t &c, uint32_t &r,
                            uint32_t out_type, uint8_t *out) {
     const uint32_t INF = 0x20000u;
     uint32_t ia = 0, ib = 0, aLo = 0, aHi = 0, bLo = 0, bHi = 0;

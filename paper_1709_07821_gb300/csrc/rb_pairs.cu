@@ -81,7 +81,7 @@ struct PairParams {
     uint32_t n_pairs;
     uint32_t small_iv;
     uint32_t prefetch;   // payload lines hinted into L2 per queued container
-    uint32_t pad;
+    uint32_t chunk;      // consecutive tiles a warp takes at once
 };
 
 // ------------------------------------------------------------ allocation
@@ -110,7 +110,26 @@ __device__ __forceinline__ uint64_t alloc_bitset_warp(ExecState *es, uint32_t la
 
 // ------------------------------------------------------------ warp paths
 
-__device__ uint64_t warp_copy(ExecState *es, const CRef &x, uint32_t lane) {
+// nw 4-byte words from S to D by the warp, 8 loads per lane in flight
+// before their stores (the compiler may not move a load above a store that
+// could alias it, so a plain loop would wait one memory latency per 128 B)
+__device__ __forceinline__ void warp_copy_words(uint32_t *D, const uint32_t *S, uint32_t nw, uint32_t lane) {
+    for (uint32_t g0 = 0; g0 < nw; g0 += 256) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t g = g0 + 32u * k + lane;
+            v[k] = g < nw ? __ldg(S + g) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t g = g0 + 32u * k + lane;
+            if (g < nw) D[g] = v[k];
+        }
+    }
+}
+
+__device__ __noinline__ uint64_t warp_copy(ExecState *es, const CRef &x, uint32_t lane) {
     if (x.type == T_BITSET) {
         uint64_t off = alloc_bitset_warp(es, lane);
         if (off == ALLOC_FAIL) return DESC_EMPTY;
@@ -126,98 +145,60 @@ __device__ uint64_t warp_copy(ExecState *es, const CRef &x, uint32_t lane) {
     uint32_t bytes = word_alloc_bytes(x.type, x.card, x.runs);
     uint64_t off = alloc_words_warp(es, bytes, lane);
     if (off == ALLOC_FAIL) return DESC_EMPTY;
-    const uint32_t *S = reinterpret_cast<const uint32_t *>(x.p);
-    uint32_t *D = reinterpret_cast<uint32_t *>(es->arena + off);
-    for (uint32_t i = lane; i < bytes / 4; i += 32) D[i] = __ldg(S + i);
+    warp_copy_words(reinterpret_cast<uint32_t *>(es->arena + off), reinterpret_cast<const uint32_t *>(x.p), bytes / 4,
+                    lane);
     return mk_desc(x.card, x.type, x.type == T_RUN ? x.runs : 0, off);
 }
 
-// a op b for one container pair by the whole warp; returns the output
-// descriptor (DESC_EMPTY for an empty result or a failed allocation)
-__device__ uint64_t warp_pair(ExecState *es, uint32_t op, const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1,
-                              uint32_t lane) {
+// a op b for one container pair whose result is a subset of an array (AND
+// with an array operand, ANDNOT with an array first), by the whole warp:
+// each value of the array is tested against the other container (Sec. 3.2
+// bit tests; a bitset is read in place, an array or run container is first
+// expanded into tile T0).  Returns the output descriptor (DESC_EMPTY for an
+// empty result or a failed allocation).
+__device__ __noinline__ uint64_t warp_probe_pair(ExecState *es, uint32_t op, const CRef &a, const CRef &b,
+                                                 uint64_t *T0, uint64_t *T1, uint32_t lane) {
     const bool a_arr = a.type == T_ARRAY, b_arr = b.type == T_ARRAY;
-    if ((op == OP_AND && (a_arr || b_arr)) || (op == OP_ANDNOT && a_arr)) {
-        // the result is a subset of an array: test each of its values
-        // against the other container (Sec. 3.2 bit tests)
-        const CRef *X, *O;
-        uint32_t want = 1;
-        if (op == OP_AND) {
-            if (a_arr && b_arr) X = a.card <= b.card ? &a : &b;
-            else X = a_arr ? &a : &b;
-            O = (X == &a) ? &b : &a;
-        } else {
-            X = &a;
-            O = &b;
-            want = 0;
-        }
-        const uint64_t *ow;
-        if (O->type == T_BITSET) {
-            ow = reinterpret_cast<const uint64_t *>(O->p);
-        } else {
-            t_decode(T0, *O, lane);
-            ow = T0;
-        }
-        uint16_t *L = reinterpret_cast<uint16_t *>(T1);
-        const uint32_t c = probe_list<true>(reinterpret_cast<const uint16_t *>(X->p), X->card, ow, want, L, lane);
-        if (c == 0) return DESC_EMPTY;
-        const uint32_t r = list_runs(L, c, lane);
-        const uint32_t ty = canon_type(c, r);
-        const uint64_t off = alloc_words_warp(es, word_alloc_bytes(ty, c, r), lane);
-        if (off == ALLOC_FAIL) return DESC_EMPTY;
-        if (ty == T_ARRAY) l_emit_array(L, c, reinterpret_cast<uint16_t *>(es->arena + off), lane);
-        else l_emit_runs(L, c, r, reinterpret_cast<uint16_t *>(T0), reinterpret_cast<uint32_t *>(es->arena + off), lane);
-        return mk_desc(c, ty, ty == T_RUN ? r : 0, off);
-    }
-    // general case: both operands as 2^16-bit words, combined word by word
-    const uint64_t *sa, *sb;
-    if (a.type == T_BITSET) sa = reinterpret_cast<const uint64_t *>(a.p);
-    else { t_decode(T0, a, lane); sa = T0; }
-    if (b.type == T_BITSET) sb = reinterpret_cast<const uint64_t *>(b.p);
-    else { t_decode(T1, b, lane); sb = T1; }
-    uint32_t c, r;
-    t_combine<true>(T0, sa, sb, op, c, r, lane);
-    __syncwarp();
-    if (c == 0) return DESC_EMPTY;
-    const uint32_t ty = canon_type(c, r);
-    uint64_t off;
-    if (ty == T_BITSET) {
-        off = alloc_bitset_warp(es, lane);
-        if (off == ALLOC_FAIL) return DESC_EMPTY;
-        t_emit_bitset(T0, reinterpret_cast<uint64_t *>(es->arena + off), lane);
+    const CRef *X, *O;
+    uint32_t want = 1;
+    if (op == OP_AND) {
+        if (a_arr && b_arr) X = a.card <= b.card ? &a : &b;
+        else X = a_arr ? &a : &b;
+        O = (X == &a) ? &b : &a;
     } else {
-        off = alloc_words_warp(es, word_alloc_bytes(ty, c, r), lane);
-        if (off == ALLOC_FAIL) return DESC_EMPTY;
-        if (ty == T_ARRAY) {
-            t_emit_array(T0, reinterpret_cast<uint16_t *>(es->arena + off), lane);
-        } else {
-            uint16_t *S = reinterpret_cast<uint16_t *>(T1);
-            t_emit_runs(T0, S, S + 2048, reinterpret_cast<uint32_t *>(es->arena + off), r, lane);
-        }
+        X = &a;
+        O = &b;
+        want = 0;
     }
+    const uint64_t *ow;
+    if (O->type == T_BITSET) {
+        ow = reinterpret_cast<const uint64_t *>(O->p);
+    } else {
+        t_decode(T0, *O, lane);
+        ow = T0;
+    }
+    uint16_t *L = reinterpret_cast<uint16_t *>(T1);
+    const uint32_t c = probe_list<true>(reinterpret_cast<const uint16_t *>(X->p), X->card, ow, want, L, lane);
+    if (c == 0) return DESC_EMPTY;
+    const uint32_t r = list_runs(L, c, lane);
+    const uint32_t ty = canon_type(c, r);
+    const uint64_t off = alloc_words_warp(es, word_alloc_bytes(ty, c, r), lane);
+    if (off == ALLOC_FAIL) return DESC_EMPTY;
+    if (ty == T_ARRAY) l_emit_array(L, c, reinterpret_cast<uint16_t *>(es->arena + off), lane);
+    else l_emit_runs(L, c, r, reinterpret_cast<uint16_t *>(T0), reinterpret_cast<uint32_t *>(es->arena + off), lane);
     return mk_desc(c, ty, ty == T_RUN ? r : 0, off);
 }
 
-// |a n b| for one container pair by the whole warp
-__device__ uint32_t warp_count_and(const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1, uint32_t lane) {
+// |a n b| for one container pair with an array operand: bit tests of the
+// smaller array's values against the other container
+__device__ __noinline__ uint32_t warp_probe_count(const CRef &a, const CRef &b, uint64_t *T0, uint32_t lane) {
     const bool a_arr = a.type == T_ARRAY, b_arr = b.type == T_ARRAY;
-    uint32_t c;
-    if (a_arr || b_arr) {
-        const CRef *X = (a_arr && b_arr) ? (a.card <= b.card ? &a : &b) : (a_arr ? &a : &b);
-        const CRef *O = (X == &a) ? &b : &a;
-        const uint64_t *ow;
-        if (O->type == T_BITSET) ow = reinterpret_cast<const uint64_t *>(O->p);
-        else { t_decode(T0, *O, lane); ow = T0; }
-        c = probe_list<false>(reinterpret_cast<const uint16_t *>(X->p), X->card, ow, 1, nullptr, lane);
-    } else {
-        const uint64_t *sa, *sb;
-        if (a.type == T_BITSET) sa = reinterpret_cast<const uint64_t *>(a.p);
-        else { t_decode(T0, a, lane); sa = T0; }
-        if (b.type == T_BITSET) sb = reinterpret_cast<const uint64_t *>(b.p);
-        else { t_decode(T1, b, lane); sb = T1; }
-        uint32_t r;
-        t_combine<false>(nullptr, sa, sb, OP_AND, c, r, lane);
-    }
+    const CRef *X = (a_arr && b_arr) ? (a.card <= b.card ? &a : &b) : (a_arr ? &a : &b);
+    const CRef *O = (X == &a) ? &b : &a;
+    const uint64_t *ow;
+    if (O->type == T_BITSET) ow = reinterpret_cast<const uint64_t *>(O->p);
+    else { t_decode(T0, *O, lane); ow = T0; }
+    const uint32_t c = probe_list<false>(reinterpret_cast<const uint16_t *>(X->p), X->card, ow, 1, nullptr, lane);
     __syncwarp();
     return c;
 }
@@ -231,6 +212,7 @@ __device__ uint32_t warp_count_and(const CRef &a, const CRef &b, uint64_t *T0, u
 __device__ __forceinline__ uint32_t merge_split(const uint16_t *ka, uint32_t na, const uint16_t *kb, uint32_t nb,
                                                 uint32_t d, uint32_t lane) {
     uint32_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+#pragma unroll 1
     while (hi > lo) {
         const uint32_t span = hi - lo;
         if (span <= 32) {
@@ -275,6 +257,7 @@ __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *
     c = 0;
     r = 0;
     const bool keep_b = (tbl & 1u) != 0;   // AND/ANDNOT stop once a is exhausted
+#pragma unroll 1
     while (i < na || (keep_b && j < nb)) {
         const uint32_t va = i < na ? (uint32_t)__ldg(a + i) : KEY_END;
         const uint32_t vb = j < nb ? (uint32_t)__ldg(b + j) : KEY_END;
@@ -301,10 +284,9 @@ __device__ __forceinline__ void prefetch_payload(const uint8_t *p, uint32_t byte
     for (uint32_t i = 0; i < n; i++) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 128 * i));
 }
 
-enum : uint32_t { M_NONE = 0, M_LANE_ARR, M_LANE_SWEEP, M_LANE_COPY, M_WARP_ARR, M_WARP_COPY, M_DEFER };
+enum : uint32_t { M_NONE = 0, M_LANE_ARR, M_LANE_SWEEP, M_COPY, M_WARP_ARR, M_DEFER };
 constexpr uint32_t WARP_MERGE_MAX = 1024;   // values of both arrays the warp merges through shared memory
 constexpr uint32_t RUN_SWEEP_MAX = 512;     // intervals one lane sweeps when runs are involved
-constexpr uint32_t LANE_COPY_MAX = 256;     // 4-byte words one lane copies
 constexpr uint32_t QCAP = 64;               // container pairs queued per warp
 
 // a container pair waiting in a warp's queue
@@ -323,30 +305,119 @@ __device__ __forceinline__ uint32_t array_result_bound(uint32_t op, uint32_t na,
     return (2 * n + 3) & ~3u;
 }
 
-// Key merge of one tile: each lane resolves its slot into a container pair,
-// an empty result or nothing.  Empty results are written at once, pairs with
-// a bitset or many values go to the heavy kernel's queue, and the others are
-// appended to the warp's item queue q (qn stays warp-uniform).
-__device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t *win, Item *q, uint32_t &qn,
-                             unsigned long long &meta, uint32_t lane) {
-    uint32_t lo = 0, hi = P.n_pairs;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (P.tile_base[mid] <= t) lo = mid;
-        else hi = mid;
+// The array and run containers that a tile's lanes copy unchanged (mine), by
+// the whole warp: one allocation in lane order, so the destination is one
+// contiguous stretch; the source is one stretch too when every copied
+// container follows the previous one (consecutive keys of one input), and
+// otherwise each destination word finds its container by a search over the
+// lanes' word offsets.  The words move 128 per round, 4 loads per lane in
+// flight; the first round is read before the allocation returns.  Writes
+// the results and adds them to the query's sums.
+__device__ __noinline__ void copy_tile(ExecState *es, PairStats *st, unsigned long long pos_base, bool mine, uint64_t dx,
+                          const uint8_t *base, uint32_t key, uint32_t pos, unsigned long long &acc, uint32_t lane) {
+    const uint32_t ty = d_type(dx), c = d_card(dx), r = ty == T_RUN ? d_runs(dx) : 0;
+    const uint32_t bytes = mine ? word_alloc_bytes(ty, c, r) : 0;
+    const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
+    const uint32_t nw = bytes / 4, wincl = incl / 4, T = total / 4;
+    const unsigned long long src = mine ? (unsigned long long)(base + d_off(dx)) : 0ull;
+    const uint32_t cm = __ballot_sync(FULL, mine);
+    const uint32_t below = cm & lanemask_lt(lane);
+    const int prev = below ? 31 - __clz(below) : (int)lane;
+    const unsigned long long pend = __shfl_sync(FULL, src + 4ull * nw, prev);
+    const bool one = __all_sync(FULL, !mine || !below || src == pend);
+    const uint32_t *S1 = reinterpret_cast<const uint32_t *>(__shfl_sync(FULL, src, __ffs(cm) - 1));
+    // word g of the tile's copies: its container is the lane j whose words
+    // [wincl_j - nw_j, wincl_j) hold g, found by a 5-step search over lanes
+    auto gather = [&](uint32_t g) -> uint32_t {
+        if (one) return g < T ? __ldg(S1 + g) : 0u;
+        uint32_t j = 0;
+#pragma unroll
+        for (uint32_t s = 16; s; s >>= 1)
+            if (__shfl_sync(FULL, wincl, j + s - 1) <= g) j += s;
+        const uint32_t *S = reinterpret_cast<const uint32_t *>(__shfl_sync(FULL, src, j));
+        const uint32_t ex = __shfl_sync(FULL, wincl - nw, j);
+        return g < T ? __ldg(S + (g - ex)) : 0u;
+    };
+    // 128 words per round, 4 loads per lane in flight; the first round is
+    // read before the allocation returns
+    unsigned long long wbase = 0;
+    bool ok = true;
+    uint32_t *D = nullptr;
+    for (uint32_t g0 = 0;; g0 += 128) {
+        uint32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = g0 + 32u * k < T ? gather(g0 + 32u * k + lane) : 0u;
+        if (g0 == 0) {
+            if (lane == 31) wbase = atomicAdd(&es->words_used, (unsigned long long)total);
+            wbase = __shfl_sync(FULL, wbase, 31);
+            ok = wbase + total <= es->words_cap;
+            if (!ok) {
+                if (lane == 0) atomicOr(&es->status, 1u);
+                break;
+            }
+            D = reinterpret_cast<uint32_t *>(es->arena + es->words_off + wbase);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (g0 + 32u * k + lane < T) D[g0 + 32u * k + lane] = v[k];
+        if (g0 + 128 >= T) break;
     }
-    const uint32_t p = lo;
+    if (mine) {
+        es->descs[pos_base + pos] = ok ? mk_desc(c, ty, r, es->words_off + wbase + incl - bytes) : DESC_EMPTY;
+        es->keys[pos_base + pos] = (uint16_t)key;
+        acc += in_payload_bytes(dx) + (ok ? payload_bytes(ty, c, r) + 10 : 0);
+    }
+    const uint32_t csum = warp_sum(mine ? c : 0);
+    if (lane == 0 && ok) {
+        atomicAdd(&st->card, (unsigned long long)csum);
+        atomicAdd(&st->words, (unsigned long long)total);
+    }
+}
+
+// Key merge of one tile: each lane resolves its slot into a container pair,
+// an empty result, a copy or nothing.  Empty results and copies of array and
+// run containers are finished at once, pairs with a bitset or many values go
+// to the heavy kernel's queue, and the others are appended to the warp's item
+// queue q (qn stays warp-uniform).
+//
+// Tiles come in chunks of consecutive ones, and the cursor carries what the
+// previous tile found: its query's tile range, so that the query is looked up
+// again only when the tile leaves it, and where its merge ended, so that the
+// merge-path search runs only for a chunk's first tile.
+struct TileCursor {
+    unsigned long long lo, hi;   // tiles of query p
+    unsigned long long t_next;   // tile whose merge starts at a's key i_next
+    uint32_t p, i_next;
+};
+
+__device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCursor &cur, uint32_t *win, Item *q,
+                             uint32_t &qn, unsigned long long &meta, uint32_t lane) {
+    if (t < cur.lo || t >= cur.hi) {
+        uint32_t lo = 0, hi = P.n_pairs;
+#pragma unroll 1
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (P.tile_base[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        cur.p = lo;
+        cur.lo = P.tile_base[lo];
+        cur.hi = lo + 1 < P.n_pairs ? P.tile_base[lo + 1] : P.n_tiles;
+    }
+    const uint32_t p = cur.p;
     const PairDev pd = P.pairs[p];
     const BmView A = P.pool[pd.a], B = P.pool[pd.b];
     ExecState *es = P.es;
     const uint32_t op = pd.op;
     const bool count_only = (pd.flags & F_COUNT) != 0;
-    const uint32_t local = (uint32_t)(t - P.tile_base[p]);
+    const uint32_t local = (uint32_t)(t - cur.lo);
 
     uint32_t kind = K_NONE, key = 0, pos = 0, ia = 0, ib = 0;
     if (pd.flags & F_MERGE) {
         const uint32_t d0 = local * 32u;
-        const uint32_t i0 = merge_split(A.keys, A.n, B.keys, B.n, d0, lane);
+        const uint32_t i0 = local == 0         ? 0u
+                            : t == cur.t_next ? cur.i_next
+                                              : merge_split(A.keys, A.n, B.keys, B.n, d0, lane);
         const uint32_t j0 = d0 - i0;
         uint32_t *WA = win;        // WA[0] = a[i0-1], WA[1..32] = a[i0..i0+31]
         uint32_t *WB = win + 33;   // WB[0..31] = b[j0..j0+31]
@@ -354,9 +425,11 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t
         WB[lane] = j0 + lane < B.n ? (uint32_t)__ldg(B.keys + j0 + lane) : KEY_END;
         if (lane == 0) WA[0] = i0 > 0 ? (uint32_t)__ldg(A.keys + i0 - 1) : 0xFFFFFFFFu;
         __syncwarp();
+        uint32_t a_upto = 0;   // a's keys among this tile's first lane + 1 elements
         if (d0 + lane < A.n + B.n) {
             // x = a's keys among this tile's first `lane` elements
             uint32_t xl = 0, xh = lane;
+#pragma unroll 1
             while (xl < xh) {
                 const uint32_t m = (xl + xh) >> 1;
                 if (WA[1 + m] <= WB[lane - 1 - m]) xl = m + 1;
@@ -364,6 +437,7 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t
             }
             const uint32_t av = WA[1 + xl], bv = WB[lane - xl];
             const uint32_t ai = i0 + xl, bj = j0 + lane - xl;
+            a_upto = xl + (av <= bv);
             if (av <= bv) {   // a's key ai; b has it too iff bv == av
                 key = av;
                 const bool m = bv == av;
@@ -383,6 +457,8 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t
                 }
             }
         }
+        cur.t_next = t + 1;
+        cur.i_next = i0 + __shfl_sync(FULL, a_upto, 31);
         __syncwarp();
     } else {
         const uint32_t slot = local * 32u + lane;
@@ -416,8 +492,8 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t
     const uint64_t db = (kind == K_PAIR || kind == K_COPY_B) ? __ldg(B.descs + ib) : 0ull;
     meta += kind == K_PAIR ? 20 : (kind == K_NONE ? 0 : 10);   // keys and descriptors read
 
-    // who does the work: one lane (array merges, run sweeps, short copies),
-    // the whole warp (large array pairs, long copies) or the heavy kernel
+    // who does the work: one lane (array merges, run sweeps), the whole warp
+    // (copies, large array pairs) or the heavy kernel
     uint32_t mode = M_NONE;
     if (kind == K_PAIR) {
         const uint32_t ta = d_type(da), tb = d_type(db);
@@ -431,9 +507,7 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t
         }
     } else if (kind == K_COPY_A || kind == K_COPY_B) {
         const uint64_t dx = kind == K_COPY_A ? da : db;
-        if (d_type(dx) == T_BITSET) mode = M_DEFER;
-        else mode = word_alloc_bytes(d_type(dx), d_card(dx), d_runs(dx)) <= 4 * LANE_COPY_MAX ? M_LANE_COPY
-                                                                                              : M_WARP_COPY;
+        mode = d_type(dx) == T_BITSET ? M_DEFER : M_COPY;
     }
     const uint32_t lm = __ballot_sync(FULL, mode == M_DEFER);
     if (lm) {
@@ -460,13 +534,15 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t
         es->descs[pd.pos_base + pos] = DESC_EMPTY;
         es->keys[pd.pos_base + pos] = (uint16_t)key;
     }
-    const bool act = mode != M_NONE && mode != M_DEFER;
+    if (__any_sync(FULL, mode == M_COPY))
+        copy_tile(es, P.stats + p, pd.pos_base, mode == M_COPY, kind == K_COPY_B ? db : da,
+                  kind == K_COPY_B ? B.base : A.base, key, pos, meta, lane);
+    const bool act = mode != M_NONE && mode != M_DEFER && mode != M_COPY;
     if (act && P.prefetch) {
         // start fetching the payloads into L2 now; the queue is processed
         // after one or two more tiles have been resolved
-        const uint64_t d1 = kind == K_COPY_B ? db : da;
-        prefetch_payload((kind == K_COPY_B ? B.base : A.base) + d_off(d1), in_payload_bytes(d1), P.prefetch);
-        if (kind == K_PAIR) prefetch_payload(B.base + d_off(db), in_payload_bytes(db), P.prefetch);
+        prefetch_payload(A.base + d_off(da), in_payload_bytes(da), P.prefetch);
+        prefetch_payload(B.base + d_off(db), in_payload_bytes(db), P.prefetch);
     }
     const uint32_t am = __ballot_sync(FULL, act);
     if (act) {
@@ -483,22 +559,61 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, uint32_t
     __syncwarp();
 }
 
+// a then b, contiguous in shared memory (na + nb <= 1024)
+__device__ __forceinline__ void stage_arrays(const uint16_t *ga, uint32_t na, const uint16_t *gb, uint32_t nb,
+                                             uint16_t *stg, uint32_t lane) {
+#pragma unroll 1
+    for (uint32_t x = lane; x < na; x += 32) stg[x] = __ldg(ga + x);
+#pragma unroll 1
+    for (uint32_t x = lane; x < nb; x += 32) stg[na + x] = __ldg(gb + x);
+    __syncwarp();
+}
+
+// |a n b| of two sorted arrays (na + nb <= 1024) by the warp, for the
+// count-only forms: staged as below, each lane walks its merge-path chunk
+// and counts the values of a that b holds too
+__device__ __noinline__ uint32_t warp_count_arrays(const uint16_t *ga, uint32_t na, const uint16_t *gb, uint32_t nb,
+                                      uint16_t *stg, uint32_t lane) {
+    stage_arrays(ga, na, gb, nb, stg, lane);
+    const uint16_t *SA = stg, *SB = stg + na;
+    const uint32_t tot = na + nb, L = (tot + 31) >> 5;
+    const uint32_t d = min(lane * L, tot), dend = min(d + L, tot);
+    uint32_t lo = d > nb ? d - nb : 0, hi = min(d, na);
+#pragma unroll 1
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (SA[m] <= SB[d - 1 - m]) lo = m + 1;
+        else hi = m;
+    }
+    uint32_t i = lo, j = d - lo, c = 0;
+#pragma unroll 1
+    for (uint32_t s = d; s < dend; s++) {
+        const uint32_t va = i < na ? (uint32_t)SA[i] : KEY_END, vb = j < nb ? (uint32_t)SB[j] : KEY_END;
+        const bool ta = va <= vb;
+        c += ta && va == vb;
+        i += ta;
+        j += !ta;
+    }
+    const uint32_t C = warp_sum(c);
+    __syncwarp();
+    return C;
+}
+
 // The warp merges two sorted arrays (na + nb <= 1024) through shared memory:
 // coalesced staging, the merged sequence cut into 32 equal chunks found by
 // merge-path binary search, one chunk per lane (recording which input each
 // step took and which values it kept), a warp scan to place the kept values,
 // and the canonical encoding.  off is the reserved output (ALLOC_FAIL: count
 // only).  Returns the descriptor; card gets the cardinality.
-__device__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, const uint16_t *ga, uint32_t na,
+__device__ __noinline__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, const uint16_t *ga, uint32_t na,
                                       const uint16_t *gb, uint32_t nb, uint16_t *stg, uint32_t lane, uint64_t off,
                                       uint32_t &card) {
+    stage_arrays(ga, na, gb, nb, stg, lane);
     uint16_t *SA = stg, *SB = stg + na, *SO = stg + WARP_MERGE_MAX;
-    for (uint32_t x = lane; x < na; x += 32) SA[x] = __ldg(ga + x);
-    for (uint32_t x = lane; x < nb; x += 32) SB[x] = __ldg(gb + x);
-    __syncwarp();
     const uint32_t tot = na + nb, L = (tot + 31) >> 5;
     const uint32_t d = min(lane * L, tot), dend = min(d + L, tot);
     uint32_t lo = d > nb ? d - nb : 0, hi = min(d, na);
+#pragma unroll 1
     while (lo < hi) {
         const uint32_t m = (lo + hi) >> 1;
         if (SA[m] <= SB[d - 1 - m]) lo = m + 1;
@@ -507,6 +622,7 @@ __device__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, const uint16_
     const uint32_t i0 = lo, j0 = d - lo;
     uint32_t i = i0, j = j0, pa = i0 > 0 ? (uint32_t)SA[i0 - 1] : 0xFFFFFFFFu;
     uint32_t take_a = 0, kept = 0, c = 0, r = 0, first = 0, last = 0xFFFFFFFEu;
+#pragma unroll 1
     for (uint32_t s = 0; d + s < dend; s++) {
         const uint32_t va = i < na ? (uint32_t)SA[i] : KEY_END, vb = j < nb ? (uint32_t)SB[j] : KEY_END;
         const bool ta = va <= vb;
@@ -544,6 +660,7 @@ __device__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, const uint16_
         uint32_t qq = cincl - c;
         i = i0;
         j = j0;
+#pragma unroll 1
         for (uint32_t s = 0; d + s < dend; s++) {
             const bool ta = (take_a >> s) & 1u;
             const uint16_t v = ta ? SA[i] : SB[j];
@@ -561,7 +678,8 @@ __device__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, const uint16_
 }
 
 // Process n <= 32 queued container pairs, one per lane (warp-sized ones by
-// the whole warp in turn), with one allocation for all their outputs.
+// the whole warp in turn), with one allocation for all their outputs.  The
+// queue holds pairs only: copies are done during the key merge.
 __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, uint16_t *stg,
                               unsigned long long &bytes_acc, uint32_t lane) {
     ExecState *es = P.es;
@@ -571,16 +689,15 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     it.p = it.pos = it.info = it.pad = 0;
     if (has) it = q[lane];
     const uint32_t mode = has ? (it.info >> 20) & 7u : M_NONE;
-    const uint32_t kind = (it.info >> 16) & 7u, key = it.info & 0xFFFFu;
+    const uint32_t key = it.info & 0xFFFFu;
     const PairDev pd = P.pairs[it.p];
     const uint8_t *abase = P.pool[pd.a].base, *bbase = P.pool[pd.b].base;
     const bool count = (pd.flags & F_COUNT) != 0;
     const uint32_t op = count ? (uint32_t)OP_AND : pd.op;
     const uint32_t tbl = keep_table(op);
-    const uint64_t dx = kind == K_COPY_B ? it.db : it.da;
-    const CRef ca = cref(kind == K_COPY_B ? bbase : abase, dx), cb = cref(bbase, it.db);
+    const CRef ca = cref(abase, it.da), cb = cref(bbase, it.db);
 
-    // sizes: exact for copies and run sweeps, the array bound for array merges
+    // sizes: exact for run sweeps, the array bound for array merges
     uint32_t bytes = 0, lc = 0, lr = 0, lt = 0;
     if (!count) {
         if (mode == M_LANE_ARR || mode == M_WARP_ARR) {
@@ -591,16 +708,10 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
                 lt = canon_type(lc, lr);
                 bytes = word_alloc_bytes(lt, lc, lr);
             }
-        } else if (mode == M_LANE_COPY || mode == M_WARP_COPY) {
-            bytes = word_alloc_bytes(ca.type, ca.card, ca.runs);
         }
     }
-    // one allocation for the batch; copies come first, in item order, so that
-    // consecutive copies of consecutive containers stay contiguous
-    const bool is_copy = mode == M_LANE_COPY || mode == M_WARP_COPY;
-    const uint32_t cbytes = is_copy ? bytes : 0, obytes = is_copy ? 0 : bytes;
-    const uint32_t cincl = warp_incl(cbytes, lane), ctotal = __shfl_sync(FULL, cincl, 31);
-    const uint32_t oincl = warp_incl(obytes, lane), total = ctotal + __shfl_sync(FULL, oincl, 31);
+    // one allocation for the batch
+    const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
     unsigned long long wbase = 0;
     bool ok = true;
     if (total) {
@@ -609,8 +720,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
         ok = wbase + total <= es->words_cap;
         if (!ok && lane == 0) atomicOr(&es->status, 1u);
     }
-    const uint64_t off = (ok && bytes) ? es->words_off + wbase + (is_copy ? cincl - cbytes : ctotal + oincl - obytes)
-                                       : ALLOC_FAIL;
+    const uint64_t off = (ok && bytes) ? es->words_off + wbase + incl - bytes : ALLOC_FAIL;
 
     uint64_t desc = DESC_EMPTY;
     uint32_t card = 0;
@@ -643,57 +753,25 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
             desc = mk_desc(lc, lt, lt == T_RUN ? lr : 0, off);
             card = lc;
         }
-    } else if (is_copy && off != ALLOC_FAIL) {
-        desc = mk_desc(ca.card, ca.type, ca.type == T_RUN ? ca.runs : 0, off);
-        card = ca.card;
-    }
-    // copies of array and run containers, by the whole warp: one coalesced
-    // memcpy when every copied container follows the previous one in both
-    // source and destination, else item by item in 32-word chunks
-    const uint32_t cm = __ballot_sync(FULL, is_copy && off != ALLOC_FAIL);
-    if (cm) {
-        const uint32_t nw = (is_copy && off != ALLOC_FAIL) ? bytes / 4 : 0;
-        const unsigned long long src = (unsigned long long)ca.p;
-        const unsigned long long dst = (unsigned long long)(es->arena + off);
-        const uint32_t below = cm & lanemask_lt(lane);
-        const int prev = below ? 31 - __clz(below) : -1;
-        const unsigned long long psrc = __shfl_sync(FULL, src, prev < 0 ? lane : prev);
-        const unsigned long long pdst = __shfl_sync(FULL, dst, prev < 0 ? lane : prev);
-        const uint32_t pnw = __shfl_sync(FULL, nw, prev < 0 ? lane : prev);
-        const bool follows = !((cm >> lane) & 1u) || prev < 0 || (src == psrc + 4ull * pnw && dst == pdst + 4ull * pnw);
-        const int first = __ffs(cm) - 1;
-        if (__all_sync(FULL, follows)) {
-            const uint32_t *S = reinterpret_cast<const uint32_t *>(__shfl_sync(FULL, src, first));
-            uint32_t *D = reinterpret_cast<uint32_t *>(__shfl_sync(FULL, dst, first));
-            const uint32_t T = warp_sum(nw);
-#pragma unroll 4
-            for (uint32_t g = lane; g < T; g += 32) D[g] = __ldg(S + g);
-        } else {
-            uint32_t q = cm;
-            while (q) {
-                const int k = __ffs(q) - 1;
-                q &= q - 1;
-                const uint32_t *S = reinterpret_cast<const uint32_t *>(__shfl_sync(FULL, src, k));
-                uint32_t *D = reinterpret_cast<uint32_t *>(__shfl_sync(FULL, dst, k));
-                const uint32_t n = __shfl_sync(FULL, nw, k);
-                for (uint32_t g = lane; g < n; g += 32) D[g] = __ldg(S + g);
-            }
-        }
     }
     // warp-sized array merges, one at a time
     uint32_t wq = __ballot_sync(FULL, mode == M_WARP_ARR);
     while (wq) {
         const int src = __ffs(wq) - 1;
         wq &= wq - 1;
-        const uint32_t m_s = __shfl_sync(FULL, mode, src), tbl_s = __shfl_sync(FULL, tbl, src);
+        const uint32_t tbl_s = __shfl_sync(FULL, tbl, src);
         const uint64_t off_s = __shfl_sync(FULL, count ? ALLOC_FAIL : off, src);
         const unsigned long long pa_s = __shfl_sync(FULL, (unsigned long long)ca.p, src);
         const unsigned long long pb_s = __shfl_sync(FULL, (unsigned long long)cb.p, src);
         const uint32_t na_s = __shfl_sync(FULL, ca.card, src), nb_s = __shfl_sync(FULL, cb.card, src);
         uint32_t c = 0;
-        const uint64_t dsc = warp_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s), na_s,
-                                               reinterpret_cast<const uint16_t *>(pb_s), nb_s, stg, lane, off_s, c);
-        (void)m_s;
+        uint64_t dsc = DESC_EMPTY;
+        if (__shfl_sync(FULL, (uint32_t)count, src))
+            c = warp_count_arrays(reinterpret_cast<const uint16_t *>(pa_s), na_s,
+                                  reinterpret_cast<const uint16_t *>(pb_s), nb_s, stg, lane);
+        else
+            dsc = warp_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s), na_s,
+                                    reinterpret_cast<const uint16_t *>(pb_s), nb_s, stg, lane, off_s, c);
         if (lane == (uint32_t)src) {
             desc = dsc;
             card = c;
@@ -712,8 +790,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
         if (wsum) atomicAdd(&P.stats[it.p].words, (unsigned long long)wsum);
     }
     if (has) {
-        bytes_acc += is_copy ? in_payload_bytes(dx)
-                                                                  : in_payload_bytes(it.da) + in_payload_bytes(it.db);
+        bytes_acc += in_payload_bytes(it.da) + in_payload_bytes(it.db);
         if (desc != DESC_EMPTY) bytes_acc += payload_bytes(d_type(desc), d_card(desc), d_runs(desc)) + 10;
     }
 }
@@ -725,17 +802,24 @@ __global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t qn = 0;
     bool done = false;
-    unsigned long long bytes_acc = 0;
+    unsigned long long bytes_acc = 0, t = 0, t_end = 0;
+    TileCursor cur;
+    cur.lo = cur.hi = 0;
+    cur.t_next = ~0ull;
+    cur.p = cur.i_next = 0;
     for (;;) {
         while (qn < 32 && !done) {
-            unsigned long long t = 0;
-            if (lane == 0) t = atomicAdd(&P.es->work, 1ull);
-            t = __shfl_sync(FULL, t, 0);
-            if (t >= P.n_tiles) {
-                done = true;
-                break;
+            if (t == t_end) {
+                if (lane == 0) t = atomicAdd(&P.es->work, (unsigned long long)P.chunk);
+                t = __shfl_sync(FULL, t, 0);
+                if (t >= P.n_tiles) {
+                    done = true;
+                    break;
+                }
+                t_end = min(t + P.chunk, P.n_tiles);
             }
-            resolve_tile(P, t, s_win[warp], s_q[warp], qn, bytes_acc, lane);
+            resolve_tile(P, t, cur, s_win[warp], s_q[warp], qn, bytes_acc, lane);
+            t++;
         }
         if (qn == 0) break;
         const uint32_t take = qn < 32 ? qn : 32;
@@ -768,7 +852,7 @@ __device__ bool tma_fail(Tma &t, ExecState *es, uint32_t lane) {
 // Stage both operands of a pair in the warp's tiles: bitsets arrive by bulk
 // copy (a -> T0, b -> T1) while the warp expands array and run operands into
 // the other tile.  False if a wait ran out.
-__device__ bool stage_pair(const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1, Tma &t, ExecState *es,
+__device__ __noinline__ bool stage_pair(const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1, Tma &t, ExecState *es,
                            uint32_t lane) {
     const uint32_t nbits = (a.type == T_BITSET) + (b.type == T_BITSET);
     if (nbits) {
@@ -791,7 +875,7 @@ __device__ bool stage_pair(const CRef &a, const CRef &b, uint64_t *T0, uint64_t 
 }
 
 // write tile T0 as a bitset container with one bulk store
-__device__ uint64_t store_bitset_tile(ExecState *es, const uint64_t *T0, uint32_t c, uint32_t lane) {
+__device__ __noinline__ uint64_t store_bitset_tile(ExecState *es, const uint64_t *T0, uint32_t c, uint32_t lane) {
     const uint64_t off = alloc_bitset_warp(es, lane);
     if (off == ALLOC_FAIL) return DESC_EMPTY;
     fence_proxy_async();
@@ -805,11 +889,11 @@ __device__ uint64_t store_bitset_tile(ExecState *es, const uint64_t *T0, uint32_
 }
 
 // a op b for one deferred container pair
-__device__ uint64_t heavy_pair(ExecState *es, uint32_t op, const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1,
+__device__ __noinline__ uint64_t heavy_pair(ExecState *es, uint32_t op, const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1,
                                Tma &t, uint32_t lane) {
     const bool a_arr = a.type == T_ARRAY, b_arr = b.type == T_ARRAY;
     if ((op == OP_AND && (a_arr || b_arr)) || (op == OP_ANDNOT && a_arr))
-        return warp_pair(es, op, a, b, T0, T1, lane);   // bit probes of an array's values
+        return warp_probe_pair(es, op, a, b, T0, T1, lane);
     if (!stage_pair(a, b, T0, T1, t, es, lane)) return DESC_EMPTY;
     uint32_t c, r;
     t_combine<true>(T0, T0, T1, op, c, r, lane);
@@ -830,7 +914,7 @@ __device__ uint64_t heavy_pair(ExecState *es, uint32_t op, const CRef &a, const 
 }
 
 // copy of a deferred container: bitsets through shared memory by bulk copy
-__device__ uint64_t heavy_copy(ExecState *es, const CRef &x, uint64_t *T0, uint64_t *T1, Tma &t, uint32_t lane) {
+__device__ __noinline__ uint64_t heavy_copy(ExecState *es, const CRef &x, uint64_t *T0, uint64_t *T1, Tma &t, uint32_t lane) {
     if (x.type != T_BITSET) return warp_copy(es, x, lane);
     (void)T1;
     fence_proxy_async();
@@ -849,9 +933,9 @@ __device__ uint64_t heavy_copy(ExecState *es, const CRef &x, uint64_t *T0, uint6
 }
 
 // |a n b| for one deferred container pair
-__device__ uint32_t heavy_count(const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1, Tma &t, ExecState *es,
+__device__ __noinline__ uint32_t heavy_count(const CRef &a, const CRef &b, uint64_t *T0, uint64_t *T1, Tma &t, ExecState *es,
                                 uint32_t lane) {
-    if (a.type == T_ARRAY || b.type == T_ARRAY) return warp_count_and(a, b, T0, T1, lane);
+    if (a.type == T_ARRAY || b.type == T_ARRAY) return warp_probe_count(a, b, T0, lane);
     if (!stage_pair(a, b, T0, T1, t, es, lane)) return 0;
     uint32_t c, r;
     t_combine<false>(nullptr, T0, T1, OP_AND, c, r, lane);
@@ -875,12 +959,20 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
     t.phase = 0;
     t.failed = false;
     const unsigned long long n = min(es->defer_n, es->defer_cap);
+    // the next item's index and record are fetched while this one is worked on
+    auto next = [&](Deferred &d) -> unsigned long long {
+        unsigned long long x = 0;
+        if (lane == 0) x = atomicAdd(&es->hwork, 1ull);
+        x = __shfl_sync(FULL, x, 0);
+        if (x < n) d = es->defer[x];
+        return x;
+    };
+    Deferred Dn;
+    unsigned long long en = next(Dn);
     for (;;) {
-        unsigned long long e = 0;
-        if (lane == 0) e = atomicAdd(&es->hwork, 1ull);
-        e = __shfl_sync(FULL, e, 0);
-        if (e >= n || t.failed) break;
-        const Deferred D = es->defer[e];
+        if (en >= n || t.failed) break;
+        const Deferred D = Dn;
+        en = next(Dn);
         const PairDev pd = P.pairs[D.p];
         const BmView A = P.pool[pd.a], B = P.pool[pd.b];
         const uint32_t kind = D.kind_key >> 16, key = D.kind_key & 0xFFFFu;
@@ -1175,7 +1267,7 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     P.n_pairs = (uint32_t)nq;
     P.small_iv = sc.small_intervals;
     P.prefetch = sc.prefetch_lines;
-    P.pad = 0;
+    P.chunk = 4;
     init_kernel_attrs();
     if ((e = cudaEventRecordWithFlags(p->ev0, s, evf)) != cudaSuccess) return e;
     if (p->total_tiles) {
