@@ -108,6 +108,42 @@ __device__ __forceinline__ uint64_t alloc_bitset_warp(ExecState *es, uint32_t la
     return es->bits_off + old;
 }
 
+// Word-region allocation for k_lean: each warp takes WCHUNK bytes at a time
+// from the shared counter and hands them out itself (state in shared memory,
+// wa[0] = next free offset, wa[1] = end of the warp's chunk); requests above
+// WDIRECT go to the counter directly.  A chunk is abandoned only when a
+// request of at most WDIRECT does not fit, so at most 1/8 of the chunked bytes
+// plus one chunk per warp go unused; the arena adds that much slack.
+// Returns the offset within the word region (warp-uniform), or ALLOC_FAIL
+// after flagging the overflow.
+constexpr uint32_t WCHUNK = 16384;
+constexpr uint32_t WDIRECT = WCHUNK / 8;
+__device__ __forceinline__ uint64_t lean_alloc(ExecState *es, unsigned long long *wa, uint32_t bytes,
+                                               uint32_t lane) {
+    unsigned long long r = 0;
+    if (lane == 0) {
+        const unsigned long long cur = wa[0], end = wa[1];
+        if (cur + bytes <= end) {
+            r = cur;
+            wa[0] = cur + bytes;
+        } else if (bytes > WDIRECT) {
+            r = atomicAdd(&es->words_used, (unsigned long long)bytes);
+            if (r + bytes > es->words_cap) r = ALLOC_FAIL;
+        } else {
+            r = atomicAdd(&es->words_used, (unsigned long long)WCHUNK);
+            if (r + WCHUNK > es->words_cap) {
+                r = ALLOC_FAIL;
+                wa[0] = wa[1] = 0;
+            } else {
+                wa[0] = r + bytes;
+                wa[1] = r + WCHUNK;
+            }
+        }
+        if (r == ALLOC_FAIL) atomicOr(&es->status, 1u);
+    }
+    return __shfl_sync(FULL, r, 0);
+}
+
 // ------------------------------------------------------------ warp paths
 
 // nw 4-byte words from S to D by the warp, 8 loads per lane in flight
@@ -313,8 +349,9 @@ __device__ __forceinline__ uint32_t array_result_bound(uint32_t op, uint32_t na,
 // lanes' word offsets.  The words move 128 per round, 4 loads per lane in
 // flight; the first round is read before the allocation returns.  Writes
 // the results and adds them to the query's sums.
-__device__ __noinline__ void copy_tile(ExecState *es, PairStats *st, unsigned long long pos_base, bool mine, uint64_t dx,
-                          const uint8_t *base, uint32_t key, uint32_t pos, unsigned long long &acc, uint32_t lane) {
+__device__ __noinline__ void copy_tile(ExecState *es, unsigned long long *wa, PairStats *st,
+                                       unsigned long long pos_base, bool mine, uint64_t dx, const uint8_t *base,
+                                       uint32_t key, uint32_t pos, unsigned long long &acc, uint32_t lane) {
     const uint32_t ty = d_type(dx), c = d_card(dx), r = ty == T_RUN ? d_runs(dx) : 0;
     const uint32_t bytes = mine ? word_alloc_bytes(ty, c, r) : 0;
     const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
@@ -348,13 +385,9 @@ __device__ __noinline__ void copy_tile(ExecState *es, PairStats *st, unsigned lo
 #pragma unroll
         for (int k = 0; k < 4; k++) v[k] = g0 + 32u * k < T ? gather(g0 + 32u * k + lane) : 0u;
         if (g0 == 0) {
-            if (lane == 31) wbase = atomicAdd(&es->words_used, (unsigned long long)total);
-            wbase = __shfl_sync(FULL, wbase, 31);
-            ok = wbase + total <= es->words_cap;
-            if (!ok) {
-                if (lane == 0) atomicOr(&es->status, 1u);
-                break;
-            }
+            wbase = lean_alloc(es, wa, total, lane);
+            ok = wbase != ALLOC_FAIL;
+            if (!ok) break;
             D = reinterpret_cast<uint32_t *>(es->arena + es->words_off + wbase);
         }
 #pragma unroll
@@ -391,7 +424,7 @@ struct TileCursor {
 };
 
 __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCursor &cur, uint32_t *win, Item *q,
-                             uint32_t &qn, unsigned long long &meta, uint32_t lane) {
+                             uint32_t &qn, unsigned long long *wa, unsigned long long &meta, uint32_t lane) {
     if (t < cur.lo || t >= cur.hi) {
         uint32_t lo = 0, hi = P.n_pairs;
 #pragma unroll 1
@@ -535,7 +568,7 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
         es->keys[pd.pos_base + pos] = (uint16_t)key;
     }
     if (__any_sync(FULL, mode == M_COPY))
-        copy_tile(es, P.stats + p, pd.pos_base, mode == M_COPY, kind == K_COPY_B ? db : da,
+        copy_tile(es, wa, P.stats + p, pd.pos_base, mode == M_COPY, kind == K_COPY_B ? db : da,
                   kind == K_COPY_B ? B.base : A.base, key, pos, meta, lane);
     const bool act = mode != M_NONE && mode != M_DEFER && mode != M_COPY;
     if (act && P.prefetch) {
@@ -680,7 +713,7 @@ __device__ __noinline__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, 
 // Process n <= 32 queued container pairs, one per lane (warp-sized ones by
 // the whole warp in turn), with one allocation for all their outputs.  The
 // queue holds pairs only: copies are done during the key merge.
-__device__ void process_items(const PairParams &P, const Item *q, uint32_t n, uint16_t *stg,
+__device__ void process_items(const PairParams &P, const Item *q, uint32_t n, uint16_t *stg, unsigned long long *wa,
                               unsigned long long &bytes_acc, uint32_t lane) {
     ExecState *es = P.es;
     const bool has = lane < n;
@@ -715,10 +748,8 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     unsigned long long wbase = 0;
     bool ok = true;
     if (total) {
-        if (lane == 31) wbase = atomicAdd(&es->words_used, (unsigned long long)total);
-        wbase = __shfl_sync(FULL, wbase, 31);
-        ok = wbase + total <= es->words_cap;
-        if (!ok && lane == 0) atomicOr(&es->status, 1u);
+        wbase = lean_alloc(es, wa, total, lane);
+        ok = wbase != ALLOC_FAIL;
     }
     const uint64_t off = (ok && bytes) ? es->words_off + wbase + incl - bytes : ALLOC_FAIL;
 
@@ -799,7 +830,10 @@ __global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
     __shared__ uint32_t s_win[LEAN_THREADS / 32][66];
     __shared__ Item s_q[LEAN_THREADS / 32][QCAP];
     __shared__ __align__(16) uint16_t s_stg[LEAN_THREADS / 32][2 * WARP_MERGE_MAX];
+    __shared__ unsigned long long s_alloc[LEAN_THREADS / 32][2];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_alloc[warp][0] = s_alloc[warp][1] = 0;
+    __syncwarp();
     uint32_t qn = 0;
     bool done = false;
     unsigned long long bytes_acc = 0, t = 0, t_end = 0;
@@ -818,12 +852,12 @@ __global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
                 }
                 t_end = min(t + P.chunk, P.n_tiles);
             }
-            resolve_tile(P, t, cur, s_win[warp], s_q[warp], qn, bytes_acc, lane);
+            resolve_tile(P, t, cur, s_win[warp], s_q[warp], qn, s_alloc[warp], bytes_acc, lane);
             t++;
         }
         if (qn == 0) break;
         const uint32_t take = qn < 32 ? qn : 32;
-        process_items(P, s_q[warp] + (qn - take), take, s_stg[warp], bytes_acc, lane);
+        process_items(P, s_q[warp] + (qn - take), take, s_stg[warp], s_alloc[warp], bytes_acc, lane);
         qn -= take;
         __syncwarp();
     }
@@ -1251,6 +1285,15 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
 // the launch sequence of one run, enqueued on stream s; when captured, the
 // events become external event-record nodes so the kernel times can still
 // be read after a graph replay
+// warps of the k_lean launch for this plan and schedule
+uint64_t lean_warps(const rb_plan *p, const rb_schedule &sc) {
+    const unsigned long long lean_cap =
+        (unsigned long long)sm_count() * (sc.lean_ctas_per_sm ? sc.lean_ctas_per_sm : 8) * (LEAN_THREADS / 32);
+    const unsigned long long warps = std::min<unsigned long long>(p->total_tiles, lean_cap);
+    return std::max<unsigned long long>(1, (warps + LEAN_THREADS / 32 - 1) / (LEAN_THREADS / 32)) *
+           (LEAN_THREADS / 32);
+}
+
 cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool capture) {
     const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
     const uint64_t nq = p->q.size();
@@ -1271,11 +1314,7 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     init_kernel_attrs();
     if ((e = cudaEventRecordWithFlags(p->ev0, s, evf)) != cudaSuccess) return e;
     if (p->total_tiles) {
-        const unsigned long long lean_cap =
-            (unsigned long long)sm_count() * (sc.lean_ctas_per_sm ? sc.lean_ctas_per_sm : 8) * (LEAN_THREADS / 32);
-        const unsigned long long warps = std::min<unsigned long long>(P.n_tiles, lean_cap);
-        const unsigned grid =
-            (unsigned)std::max<unsigned long long>(1, (warps + LEAN_THREADS / 32 - 1) / (LEAN_THREADS / 32));
+        const unsigned grid = (unsigned)(lean_warps(p, sc) / (LEAN_THREADS / 32));
         k_lean<<<grid, LEAN_THREADS, 0, s>>>(P);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1301,14 +1340,17 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
 
 struct ArenaLayout {
     uint64_t o_keys, o_defer, o_words, o_bits, bytes;
+    uint64_t words_cap;   // word region incl. the slack of k_lean's per-warp chunks
 };
+
 ArenaLayout arena_layout(const rb_plan *p) {
     ArenaLayout L;
     const uint64_t T = p->total_pos;
     L.o_keys = align_up(8 * T, 256);
     L.o_defer = align_up(L.o_keys + 2 * T, 256);
     L.o_words = align_up(L.o_defer + sizeof(Deferred) * p->defer_cap, 256);
-    L.o_bits = align_up(L.o_words + p->words_cap, 256);
+    L.words_cap = p->words_cap + p->words_cap / 7 + lean_warps(p, current_schedule()) * WCHUNK;
+    L.o_bits = align_up(L.o_words + L.words_cap, 256);
     L.bytes = L.o_bits + p->bits_cap;
     return L;
 }
@@ -1333,7 +1375,7 @@ rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool
     h.defer = (Deferred *)((uint8_t *)a->ptr + L.o_defer);
     h.defer_cap = p->defer_cap;
     h.words_off = L.o_words;
-    h.words_cap = p->words_cap;
+    h.words_cap = L.words_cap;
     h.bits_off = L.o_bits;
     h.bits_cap = p->bits_cap;
     cudaError_t e = cudaSuccess;
