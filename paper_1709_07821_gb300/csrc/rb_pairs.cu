@@ -110,7 +110,8 @@ __device__ __forceinline__ uint64_t alloc_bitset_warp(ExecState *es, uint32_t la
 
 // Word-region allocation for k_lean: each warp takes WCHUNK bytes at a time
 // from the shared counter and hands them out itself (state in shared memory,
-// wa[0] = next free offset, wa[1] = end of the warp's chunk); requests above
+// wa[0] = next free offset, wa[1] = end of the warp's chunk; wa[2], wa[3]
+// gather the current query's cardinality and word bytes); requests above
 // WDIRECT go to the counter directly.  A chunk is abandoned only when a
 // request of at most WDIRECT does not fit, so at most 1/8 of the chunked bytes
 // plus one chunk per warp go unused; the arena adds that much slack.
@@ -349,9 +350,9 @@ __device__ __forceinline__ uint32_t array_result_bound(uint32_t op, uint32_t na,
 // lanes' word offsets.  The words move 128 per round, 4 loads per lane in
 // flight; the first round is read before the allocation returns.  Writes
 // the results and adds them to the query's sums.
-__device__ __noinline__ void copy_tile(ExecState *es, unsigned long long *wa, PairStats *st,
-                                       unsigned long long pos_base, bool mine, uint64_t dx, const uint8_t *base,
-                                       uint32_t key, uint32_t pos, unsigned long long &acc, uint32_t lane) {
+__device__ __noinline__ void copy_tile(ExecState *es, unsigned long long *wa, unsigned long long pos_base, bool mine,
+                                       uint64_t dx, const uint8_t *base, uint32_t key, uint32_t pos,
+                                       unsigned long long &acc, uint32_t lane) {
     const uint32_t ty = d_type(dx), c = d_card(dx), r = ty == T_RUN ? d_runs(dx) : 0;
     const uint32_t bytes = mine ? word_alloc_bytes(ty, c, r) : 0;
     const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
@@ -400,11 +401,23 @@ __device__ __noinline__ void copy_tile(ExecState *es, unsigned long long *wa, Pa
         es->keys[pos_base + pos] = (uint16_t)key;
         acc += in_payload_bytes(dx) + (ok ? payload_bytes(ty, c, r) + 10 : 0);
     }
+    // the query's sums gather in the warp's shared state (wa[2], wa[3]) and
+    // are flushed when the warp leaves the query
     const uint32_t csum = warp_sum(mine ? c : 0);
     if (lane == 0 && ok) {
-        atomicAdd(&st->card, (unsigned long long)csum);
-        atomicAdd(&st->words, (unsigned long long)total);
+        wa[2] += csum;
+        wa[3] += total;
     }
+}
+
+// add the sums a warp gathered for query p to its stats
+__device__ __forceinline__ void flush_sums(PairStats *stats, uint32_t p, unsigned long long *wa, uint32_t lane) {
+    if (lane == 0) {
+        if (wa[2]) atomicAdd(&stats[p].card, wa[2]);
+        if (wa[3]) atomicAdd(&stats[p].words, wa[3]);
+        wa[2] = wa[3] = 0;
+    }
+    __syncwarp();
 }
 
 // Key merge of one tile: each lane resolves its slot into a container pair,
@@ -426,6 +439,7 @@ struct TileCursor {
 __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCursor &cur, uint32_t *win, Item *q,
                              uint32_t &qn, unsigned long long *wa, unsigned long long &meta, uint32_t lane) {
     if (t < cur.lo || t >= cur.hi) {
+        flush_sums(P.stats, cur.p, wa, lane);
         uint32_t lo = 0, hi = P.n_pairs;
 #pragma unroll 1
         while (hi - lo > 1) {
@@ -568,7 +582,7 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
         es->keys[pd.pos_base + pos] = (uint16_t)key;
     }
     if (__any_sync(FULL, mode == M_COPY))
-        copy_tile(es, wa, P.stats + p, pd.pos_base, mode == M_COPY, kind == K_COPY_B ? db : da,
+        copy_tile(es, wa, pd.pos_base, mode == M_COPY, kind == K_COPY_B ? db : da,
                   kind == K_COPY_B ? B.base : A.base, key, pos, meta, lane);
     const bool act = mode != M_NONE && mode != M_DEFER && mode != M_COPY;
     if (act && P.prefetch) {
@@ -830,9 +844,9 @@ __global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
     __shared__ uint32_t s_win[LEAN_THREADS / 32][66];
     __shared__ Item s_q[LEAN_THREADS / 32][QCAP];
     __shared__ __align__(16) uint16_t s_stg[LEAN_THREADS / 32][2 * WARP_MERGE_MAX];
-    __shared__ unsigned long long s_alloc[LEAN_THREADS / 32][2];
+    __shared__ unsigned long long s_alloc[LEAN_THREADS / 32][4];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_alloc[warp][0] = s_alloc[warp][1] = 0;
+    if (lane == 0) s_alloc[warp][0] = s_alloc[warp][1] = s_alloc[warp][2] = s_alloc[warp][3] = 0;
     __syncwarp();
     uint32_t qn = 0;
     bool done = false;
@@ -861,6 +875,7 @@ __global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
         qn -= take;
         __syncwarp();
     }
+    flush_sums(P.stats, cur.p, s_alloc[warp], lane);
     const unsigned long long tot = warp_sum64(bytes_acc);
     if (lane == 0 && tot) atomicAdd(&P.es->lean_bytes, tot);
 }
