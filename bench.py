@@ -48,6 +48,35 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_sha256():
+    """SHA-256 of the pairwise kernels' sources without their comment-only
+    lines (csrc/rb_pairs.cu, rb_device.cuh, rb_internal.h, in that order)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("rb_pairs.cu", "rb_device.cuh", "rb_internal.h"):
+        with open(os.path.join(ROOT, "paper_1709_07821_gb300", "csrc", f)) as fh:
+            for line in fh:
+                if not line.strip().startswith("//"):
+                    h.update(line.encode())
+    return h.hexdigest()
+
+
+def lean_traffic(alg_bytes):
+    """DRAM bytes of one materialising k_lean launch: the dram/algorithmic
+    byte ratio of the ncu capture summarised in profiles/ times this
+    launch's algorithmic bytes, or None when the kernel sources differ from
+    those the capture was taken from (or there is no capture)."""
+    import hashlib
+    import re
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "k_lean_batched_512pool_8192pairs.md")).read()
+        ratio = float(re.search(r"^traffic_ratio: ([0-9.]+)", txt, re.M).group(1))
+        want = re.search(r"^source_sha256: ([0-9a-f]{64})", txt, re.M).group(1)
+        return ratio * alg_bytes if kernel_source_sha256() == want else None
+    except Exception:
+        return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -346,7 +375,8 @@ def run_ours(args):
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     stage_gbs = (lean_b + heavy_b) / ((lean_ms + heavy_ms) / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": args.traffic, "kernel": dom, "kernel_ms": kernel_ms,
+                "traffic": args.traffic if args.traffic is not None else (
+                    lean_traffic(alg_bytes) if dom.startswith("k_lean") else None), "kernel": dom, "kernel_ms": kernel_ms,
                 "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
                 "pair_stage": {"lean_ms": lean_ms, "heavy_ms": heavy_ms, "lean_bytes": lean_b,
                                "heavy_bytes": heavy_b, "achieved_gbs": stage_gbs, "frac": stage_gbs / peak,

@@ -18,11 +18,14 @@
 // position empty), a's key index for AND/ANDNOT.  Every position of a query's
 // output range is written exactly once, so compaction only drops empties.
 //
-// Kernels.  k_lean (high occupancy, no shared tiles) does the key merge of a
-// tile and finishes every small container pair with a one-lane interval sweep;
-// pairs with a bitset or many values/runs go to a deferred queue that k_heavy
-// (one warp per pair, two 8 KB shared tiles per warp) drains.  k_compact then
-// drops the empty results of every query.
+// Kernels.  k_lean (high occupancy, small shared buffers) does the key merge
+// of a tile, copies the tile's unmatched array and run containers with the
+// whole warp, and queues its container pairs; each batch of 32 queued pairs
+// is finished one pair per lane (small array merges, run sweeps) or by the
+// whole warp in turn (array pairs up to 1024 values).  Pairs with a bitset or
+// more values go to a deferred queue that k_heavy (one warp per pair, two
+// 8 KB shared tiles per warp, bitsets moved by bulk copies) drains.
+// k_compact then drops the empty results of every query.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
