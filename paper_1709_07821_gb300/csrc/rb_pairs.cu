@@ -885,12 +885,36 @@ __global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
 
 // ------------------------------------------------------------ heavy kernel
 
-// bulk-copy state of one heavy-kernel warp
+// bulk-copy state of one heavy-kernel warp, and the warp's current chunk of
+// the bitset region ([bcur, bend), taken HCHUNK bitsets at a time)
 struct Tma {
     uint64_t *bar;
     uint32_t phase;
     bool failed;
+    unsigned long long bcur, bend;
 };
+constexpr uint32_t HCHUNK = 8;
+
+// one 8 KB slot of the bitset region for the warp: from its chunk, or a new
+// chunk from the shared counter (at most HCHUNK - 1 slots per warp go unused;
+// the arena adds that slack)
+__device__ __forceinline__ uint64_t heavy_alloc_bitset(ExecState *es, Tma &t, uint32_t lane) {
+    if (t.bcur + 8192ull > t.bend) {
+        unsigned long long old = 0;
+        if (lane == 0) old = atomicAdd(&es->bits_used, 8192ull * HCHUNK);
+        old = __shfl_sync(FULL, old, 0);
+        if (old + 8192ull * HCHUNK > es->bits_cap) {
+            if (lane == 0) atomicOr(&es->status, 1u);
+            t.bcur = t.bend = 0;
+            return ALLOC_FAIL;
+        }
+        t.bcur = old;
+        t.bend = old + 8192ull * HCHUNK;
+    }
+    const uint64_t off = es->bits_off + t.bcur;
+    t.bcur += 8192ull;
+    return off;
+}
 
 // a wait ran out: record it, give the copy in flight one more bounded wait,
 // and stop using the tiles
@@ -927,8 +951,9 @@ __device__ __noinline__ bool stage_pair(const CRef &a, const CRef &b, uint64_t *
 }
 
 // write tile T0 as a bitset container with one bulk store
-__device__ __noinline__ uint64_t store_bitset_tile(ExecState *es, const uint64_t *T0, uint32_t c, uint32_t lane) {
-    const uint64_t off = alloc_bitset_warp(es, lane);
+__device__ __noinline__ uint64_t store_bitset_tile(ExecState *es, Tma &t, const uint64_t *T0, uint32_t c,
+                                                   uint32_t lane) {
+    const uint64_t off = heavy_alloc_bitset(es, t, lane);
     if (off == ALLOC_FAIL) return DESC_EMPTY;
     fence_proxy_async();
     __syncwarp();
@@ -952,7 +977,7 @@ __device__ __noinline__ uint64_t heavy_pair(ExecState *es, uint32_t op, const CR
     __syncwarp();
     if (c == 0) return DESC_EMPTY;
     const uint32_t ty = canon_type(c, r);
-    if (ty == T_BITSET) return store_bitset_tile(es, T0, c, lane);
+    if (ty == T_BITSET) return store_bitset_tile(es, t, T0, c, lane);
     const uint64_t off = alloc_words_warp(es, word_alloc_bytes(ty, c, r), lane);
     if (off == ALLOC_FAIL) return DESC_EMPTY;
     if (ty == T_ARRAY) {
@@ -981,7 +1006,7 @@ __device__ __noinline__ uint64_t heavy_copy(ExecState *es, const CRef &x, uint64
         tma_fail(t, es, lane);
         return DESC_EMPTY;
     }
-    return store_bitset_tile(es, T0, x.card, lane);
+    return store_bitset_tile(es, t, T0, x.card, lane);
 }
 
 // |a n b| for one deferred container pair
@@ -1010,6 +1035,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
     t.bar = &s_bar[warp];
     t.phase = 0;
     t.failed = false;
+    t.bcur = t.bend = 0;
+    unsigned long long hbytes = 0;   // algorithmic bytes of this warp's items (lane 0)
     const unsigned long long n = min(es->defer_n, es->defer_cap);
     // the next item's index and record are fetched while this one is worked on
     auto next = [&](Deferred &d) -> unsigned long long {
@@ -1032,9 +1059,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
         if (pd.flags & F_COUNT) {
             const uint32_t c = heavy_count(cref(A.base, D.da), cref(B.base, D.db), T0, T1, t, es, lane);
             if (lane == 0) {
-                const unsigned long long ib = in_payload_bytes(D.da) + in_payload_bytes(D.db);
                 if (c) atomicAdd(&S->card, (unsigned long long)c);
-                atomicAdd(&es->heavy_bytes, ib);
+                hbytes += in_payload_bytes(D.da) + in_payload_bytes(D.db);
             }
             __syncwarp();
             continue;
@@ -1059,10 +1085,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
                 else atomicAdd(&S->words, (unsigned long long)word_alloc_bytes(ty, c, r));
                 ib += payload_bytes(ty, c, r) + 10;
             }
-            atomicAdd(&es->heavy_bytes, ib);
+            hbytes += ib;
         }
         __syncwarp();
     }
+    if (lane == 0 && hbytes) atomicAdd(&es->heavy_bytes, hbytes);
     // every bulk store of this warp has completed before the kernel ends
     if (lane == 0) bulk_wait_all();
     __syncwarp();
@@ -1303,6 +1330,12 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
 // the launch sequence of one run, enqueued on stream s; when captured, the
 // events become external event-record nodes so the kernel times can still
 // be read after a graph replay
+// warps of the k_heavy launch for this schedule that can take deferred pairs
+uint64_t heavy_warps(const rb_plan *p, const rb_schedule &sc) {
+    const uint64_t w = (uint64_t)sm_count() * std::max<uint32_t>(1, sc.ctas_per_sm) * sc.warps_per_cta;
+    return std::min<uint64_t>(w, p->defer_cap);
+}
+
 // warps of the k_lean launch for this plan and schedule
 uint64_t lean_warps(const rb_plan *p, const rb_schedule &sc) {
     const unsigned long long lean_cap =
@@ -1359,6 +1392,7 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
 struct ArenaLayout {
     uint64_t o_keys, o_defer, o_words, o_bits, bytes;
     uint64_t words_cap;   // word region incl. the slack of k_lean's per-warp chunks
+    uint64_t bits_cap;    // bitset region incl. the slack of k_heavy's per-warp chunks
 };
 
 ArenaLayout arena_layout(const rb_plan *p) {
@@ -1369,7 +1403,8 @@ ArenaLayout arena_layout(const rb_plan *p) {
     L.o_words = align_up(L.o_defer + sizeof(Deferred) * p->defer_cap, 256);
     L.words_cap = p->words_cap + p->words_cap / 7 + lean_warps(p, current_schedule()) * WCHUNK;
     L.o_bits = align_up(L.o_words + L.words_cap, 256);
-    L.bytes = L.o_bits + p->bits_cap;
+    L.bits_cap = p->bits_cap + heavy_warps(p, current_schedule()) * (HCHUNK - 1) * 8192ull;
+    L.bytes = L.o_bits + L.bits_cap;
     return L;
 }
 
@@ -1395,7 +1430,7 @@ rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool
     h.words_off = L.o_words;
     h.words_cap = L.words_cap;
     h.bits_off = L.o_bits;
-    h.bits_cap = p->bits_cap;
+    h.bits_cap = L.bits_cap;
     cudaError_t e = cudaSuccess;
     if (graph) {
         if (!p->ps) e = cudaStreamCreateWithFlags(&p->ps, cudaStreamNonBlocking);
