@@ -148,6 +148,34 @@ __device__ __forceinline__ uint64_t lean_alloc(ExecState *es, unsigned long long
     return __shfl_sync(FULL, r, 0);
 }
 
+// The same scheme for k_heavy, whose chunk state is warp-uniform registers;
+// returns the absolute arena offset, or ALLOC_FAIL after flagging overflow.
+struct WChunk {
+    unsigned long long cur, end;
+};
+__device__ __forceinline__ uint64_t chunk_alloc_words(ExecState *es, WChunk &w, uint32_t bytes, uint32_t lane) {
+    if (w.cur + bytes <= w.end) {
+        const uint64_t r = w.cur;
+        w.cur += bytes;
+        return es->words_off + r;
+    }
+    const bool direct = bytes > WDIRECT;
+    const uint32_t take = direct ? bytes : WCHUNK;
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(&es->words_used, (unsigned long long)take);
+    old = __shfl_sync(FULL, old, 0);
+    if (old + take > es->words_cap) {
+        if (lane == 0) atomicOr(&es->status, 1u);
+        if (!direct) w.cur = w.end = 0;
+        return ALLOC_FAIL;
+    }
+    if (!direct) {
+        w.cur = old + bytes;
+        w.end = old + WCHUNK;
+    }
+    return es->words_off + old;
+}
+
 // ------------------------------------------------------------ warp paths
 
 // nw 4-byte words from S to D by the warp, 8 loads per lane in flight
@@ -196,8 +224,8 @@ __device__ __noinline__ uint64_t warp_copy(ExecState *es, const CRef &x, uint32_
 // bit tests; a bitset is read in place, an array or run container is first
 // expanded into tile T0).  Returns the output descriptor (DESC_EMPTY for an
 // empty result or a failed allocation).
-__device__ __noinline__ uint64_t warp_probe_pair(ExecState *es, uint32_t op, const CRef &a, const CRef &b,
-                                                 uint64_t *T0, uint64_t *T1, uint32_t lane) {
+__device__ __noinline__ uint64_t warp_probe_pair(ExecState *es, WChunk &wc, uint32_t op, const CRef &a,
+                                                 const CRef &b, uint64_t *T0, uint64_t *T1, uint32_t lane) {
     const bool a_arr = a.type == T_ARRAY, b_arr = b.type == T_ARRAY;
     const CRef *X, *O;
     uint32_t want = 1;
@@ -222,7 +250,7 @@ __device__ __noinline__ uint64_t warp_probe_pair(ExecState *es, uint32_t op, con
     if (c == 0) return DESC_EMPTY;
     const uint32_t r = list_runs(L, c, lane);
     const uint32_t ty = canon_type(c, r);
-    const uint64_t off = alloc_words_warp(es, word_alloc_bytes(ty, c, r), lane);
+    const uint64_t off = chunk_alloc_words(es, wc, word_alloc_bytes(ty, c, r), lane);
     if (off == ALLOC_FAIL) return DESC_EMPTY;
     if (ty == T_ARRAY) l_emit_array(L, c, reinterpret_cast<uint16_t *>(es->arena + off), lane);
     else l_emit_runs(L, c, r, reinterpret_cast<uint16_t *>(T0), reinterpret_cast<uint32_t *>(es->arena + off), lane);
@@ -892,6 +920,7 @@ struct Tma {
     uint32_t phase;
     bool failed;
     unsigned long long bcur, bend;
+    WChunk wc;   // the warp's chunk of the word region
 };
 constexpr uint32_t HCHUNK = 8;
 
@@ -970,7 +999,7 @@ __device__ __noinline__ uint64_t heavy_pair(ExecState *es, uint32_t op, const CR
                                Tma &t, uint32_t lane) {
     const bool a_arr = a.type == T_ARRAY, b_arr = b.type == T_ARRAY;
     if ((op == OP_AND && (a_arr || b_arr)) || (op == OP_ANDNOT && a_arr))
-        return warp_probe_pair(es, op, a, b, T0, T1, lane);
+        return warp_probe_pair(es, t.wc, op, a, b, T0, T1, lane);
     if (!stage_pair(a, b, T0, T1, t, es, lane)) return DESC_EMPTY;
     uint32_t c, r;
     t_combine<true>(T0, T0, T1, op, c, r, lane);
@@ -978,7 +1007,7 @@ __device__ __noinline__ uint64_t heavy_pair(ExecState *es, uint32_t op, const CR
     if (c == 0) return DESC_EMPTY;
     const uint32_t ty = canon_type(c, r);
     if (ty == T_BITSET) return store_bitset_tile(es, t, T0, c, lane);
-    const uint64_t off = alloc_words_warp(es, word_alloc_bytes(ty, c, r), lane);
+    const uint64_t off = chunk_alloc_words(es, t.wc, word_alloc_bytes(ty, c, r), lane);
     if (off == ALLOC_FAIL) return DESC_EMPTY;
     if (ty == T_ARRAY) {
         t_emit_array(T0, reinterpret_cast<uint16_t *>(es->arena + off), lane);
@@ -1036,6 +1065,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
     t.phase = 0;
     t.failed = false;
     t.bcur = t.bend = 0;
+    t.wc.cur = t.wc.end = 0;
     unsigned long long hbytes = 0;   // algorithmic bytes of this warp's items (lane 0)
     const unsigned long long n = min(es->defer_n, es->defer_cap);
     // the next item's index and record are fetched while this one is worked on
@@ -1401,7 +1431,8 @@ ArenaLayout arena_layout(const rb_plan *p) {
     L.o_keys = align_up(8 * T, 256);
     L.o_defer = align_up(L.o_keys + 2 * T, 256);
     L.o_words = align_up(L.o_defer + sizeof(Deferred) * p->defer_cap, 256);
-    L.words_cap = p->words_cap + p->words_cap / 7 + lean_warps(p, current_schedule()) * WCHUNK;
+    const rb_schedule sc = current_schedule();
+    L.words_cap = p->words_cap + p->words_cap / 7 + (lean_warps(p, sc) + heavy_warps(p, sc)) * WCHUNK;
     L.o_bits = align_up(L.o_words + L.words_cap, 256);
     L.bits_cap = p->bits_cap + heavy_warps(p, current_schedule()) * (HCHUNK - 1) * 8192ull;
     L.bytes = L.o_bits + L.bits_cap;
