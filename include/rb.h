@@ -166,9 +166,13 @@ rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream)
 /* Measurements of the last run, from CUDA events on the stream the kernels
  * ran on: the container-pair stage is a lean kernel (key merge, small pairs)
  * then a heavy kernel (pairs deferred by the lean one: bitsets, many values
- * or runs).  *_bytes are the algorithmic bytes each kernel moved (input and
- * output payloads, 10 bytes of key + descriptor per container), counted by
- * the kernels themselves; deferred is the number of deferred pairs. */
+ * or runs).  *_bytes are the algorithmic bytes of each kernel's share of the
+ * work: the input payloads the op must read (AND: matched containers; OR,
+ * XOR: every container; ANDNOT: all of a, matched of b) and the output
+ * payloads, counted by the kernels themselves, plus 15 bytes of key and
+ * metadata per container of both inputs (lean kernel) and per output
+ * container, and 8 bytes per count-only result; deferred is the number of
+ * deferred pairs. */
 typedef struct {
     double lean_ms, heavy_ms;
     uint64_t lean_bytes, heavy_bytes, alg_bytes, out_bytes, deferred;

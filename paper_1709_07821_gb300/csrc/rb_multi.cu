@@ -172,13 +172,13 @@ __device__ void multi_tile(const MParams &P, unsigned long long t, uint64_t *T0,
             find_key(D, k_key, j);
             const uint64_t d0 = __ldg(D.descs + j);
             t_decode(T0, cref(D.base, d0), lane);
-            in_acc += in_payload_bytes(d0) + 10;
+            in_acc += in_payload_bytes(d0) + 15;
             for (uint32_t i = 0; i < qd.k; i++) {
                 if (i == qd.driver) continue;
                 const BmView V = P.pool[mem[i]];
                 find_key(V, k_key, j);
                 const uint64_t d = __ldg(V.descs + j);
-                in_acc += in_payload_bytes(d) + 10;
+                in_acc += in_payload_bytes(d) + 15;
                 fold_into(T0, T1, cref(V.base, d), OP_AND, lane);
             }
         } else {
@@ -189,7 +189,7 @@ __device__ void multi_tile(const MParams &P, unsigned long long t, uint64_t *T0,
                 uint32_t j;
                 if (!find_key(V, k_key, j)) continue;
                 const uint64_t d = __ldg(V.descs + j);
-                in_acc += in_payload_bytes(d) + 10;
+                in_acc += in_payload_bytes(d) + 15;
                 fold_into(T0, T1, cref(V.base, d), OP_OR, lane);
             }
         }

@@ -42,6 +42,10 @@ constexpr uint32_t F_COUNT = 1, F_MERGE = 2;
 enum : uint32_t { K_NONE = 0, K_EMPTY = 1, K_PAIR = 2, K_COPY_A = 3, K_COPY_B = 4 };
 constexpr int LEAN_THREADS = 128;
 constexpr uint32_t KEY_END = 0x10000u;   // past-the-end key sentinel
+// algorithmic bytes of a container's key and metadata (key 2, type 1,
+// cardinality 4, payload offset 8), whatever the layout packs them into,
+// and of a count-only result
+constexpr uint32_t META_BYTES = 15, COUNT_BYTES = 8;
 
 struct PairDev {
     uint32_t a, b, op, flags;
@@ -430,7 +434,7 @@ __device__ __noinline__ void copy_tile(ExecState *es, unsigned long long *wa, un
     if (mine) {
         es->descs[pos_base + pos] = ok ? mk_desc(c, ty, r, es->words_off + wbase + incl - bytes) : DESC_EMPTY;
         es->keys[pos_base + pos] = (uint16_t)key;
-        acc += in_payload_bytes(dx) + (ok ? payload_bytes(ty, c, r) + 10 : 0);
+        acc += in_payload_bytes(dx) + (ok ? payload_bytes(ty, c, r) + META_BYTES : 0);
     }
     // the query's sums gather in the warp's shared state (wa[2], wa[3]) and
     // are flushed when the warp leaves the query
@@ -568,7 +572,6 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
     }
     const uint64_t da = (kind == K_PAIR || kind == K_COPY_A) ? __ldg(A.descs + ia) : 0ull;
     const uint64_t db = (kind == K_PAIR || kind == K_COPY_B) ? __ldg(B.descs + ib) : 0ull;
-    meta += kind == K_PAIR ? 20 : (kind == K_NONE ? 0 : 10);   // keys and descriptors read
 
     // who does the work: one lane (array merges, run sweeps), the whole warp
     // (copies, large array pairs) or the heavy kernel
@@ -577,7 +580,7 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
         const uint32_t ta = d_type(da), tb = d_type(db);
         if (ta == T_ARRAY && tb == T_ARRAY) {
             const uint32_t n = d_card(da) + d_card(db);
-            mode = n <= P.small_iv ? M_LANE_ARR : n <= WARP_MERGE_MAX ? M_WARP_ARR : M_DEFER;
+            mode = n <= P.small_iv ? M_LANE_ARR : n <= WARP_MERGE_MAX - 2 ? M_WARP_ARR : M_DEFER;
         } else if (ta != T_BITSET && tb != T_BITSET && n_intervals(da) + n_intervals(db) <= RUN_SWEEP_MAX) {
             mode = M_LANE_SWEEP;
         } else {
@@ -637,23 +640,43 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
     __syncwarp();
 }
 
-// a then b, contiguous in shared memory (na + nb <= 1024)
-__device__ __forceinline__ void stage_arrays(const uint16_t *ga, uint32_t na, const uint16_t *gb, uint32_t nb,
-                                             uint16_t *stg, uint32_t lane) {
-#pragma unroll 1
-    for (uint32_t x = lane; x < na; x += 32) stg[x] = __ldg(ga + x);
-#pragma unroll 1
-    for (uint32_t x = lane; x < nb; x += 32) stg[na + x] = __ldg(gb + x);
-    __syncwarp();
+// The first 32 four-byte words of both arrays of a warp-sized pair, one per
+// lane, loaded ahead: the warp requests the next pair's while it merges the
+// current one.  Array payloads start 4-byte aligned and are padded to 4 bytes.
+struct WPre {
+    uint32_t a, b;
+};
+__device__ __forceinline__ WPre prefetch_words(const uint16_t *ga, uint32_t na, const uint16_t *gb, uint32_t nb,
+                                               uint32_t lane) {
+    WPre w;
+    w.a = lane < (na + 1) / 2 ? __ldg(reinterpret_cast<const uint32_t *>(ga) + lane) : 0u;
+    w.b = lane < (nb + 1) / 2 ? __ldg(reinterpret_cast<const uint32_t *>(gb) + lane) : 0u;
+    return w;
 }
 
-// |a n b| of two sorted arrays (na + nb <= 1024) by the warp, for the
+// a then b in shared memory as whole words (b starts at element 2 * ceil(na / 2);
+// na + nb <= 1022 fits 1024 elements), from the prefetched words and the rest
+// of the arrays; returns b's start
+__device__ __forceinline__ uint16_t *stage_words(const uint16_t *ga, uint32_t na, const uint16_t *gb, uint32_t nb,
+                                                 const WPre &w, uint16_t *stg, uint32_t lane) {
+    const uint32_t wa = (na + 1) / 2, wb = (nb + 1) / 2;
+    uint32_t *SA = reinterpret_cast<uint32_t *>(stg), *SB = SA + wa;
+    if (lane < wa) SA[lane] = w.a;
+    if (lane < wb) SB[lane] = w.b;
+#pragma unroll 1
+    for (uint32_t x = 32 + lane; x < wa; x += 32) SA[x] = __ldg(reinterpret_cast<const uint32_t *>(ga) + x);
+#pragma unroll 1
+    for (uint32_t x = 32 + lane; x < wb; x += 32) SB[x] = __ldg(reinterpret_cast<const uint32_t *>(gb) + x);
+    __syncwarp();
+    return stg + 2 * wa;
+}
+
+// |a n b| of two sorted arrays (na + nb <= 1022) by the warp, for the
 // count-only forms: staged as below, each lane walks its merge-path chunk
 // and counts the values of a that b holds too
 __device__ __noinline__ uint32_t warp_count_arrays(const uint16_t *ga, uint32_t na, const uint16_t *gb, uint32_t nb,
-                                      uint16_t *stg, uint32_t lane) {
-    stage_arrays(ga, na, gb, nb, stg, lane);
-    const uint16_t *SA = stg, *SB = stg + na;
+                                                   const WPre &w, uint16_t *stg, uint32_t lane) {
+    const uint16_t *SA = stg, *SB = stage_words(ga, na, gb, nb, w, stg, lane);
     const uint32_t tot = na + nb, L = (tot + 31) >> 5;
     const uint32_t d = min(lane * L, tot), dend = min(d + L, tot);
     uint32_t lo = d > nb ? d - nb : 0, hi = min(d, na);
@@ -677,17 +700,16 @@ __device__ __noinline__ uint32_t warp_count_arrays(const uint16_t *ga, uint32_t 
     return C;
 }
 
-// The warp merges two sorted arrays (na + nb <= 1024) through shared memory:
+// The warp merges two sorted arrays (na + nb <= 1022) through shared memory:
 // coalesced staging, the merged sequence cut into 32 equal chunks found by
 // merge-path binary search, one chunk per lane (recording which input each
 // step took and which values it kept), a warp scan to place the kept values,
 // and the canonical encoding.  off is the reserved output (ALLOC_FAIL: count
 // only).  Returns the descriptor; card gets the cardinality.
 __device__ __noinline__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, const uint16_t *ga, uint32_t na,
-                                      const uint16_t *gb, uint32_t nb, uint16_t *stg, uint32_t lane, uint64_t off,
-                                      uint32_t &card) {
-    stage_arrays(ga, na, gb, nb, stg, lane);
-    uint16_t *SA = stg, *SB = stg + na, *SO = stg + WARP_MERGE_MAX;
+                                                   const uint16_t *gb, uint32_t nb, const WPre &w, uint16_t *stg,
+                                                   uint32_t lane, uint64_t off, uint32_t &card) {
+    uint16_t *SA = stg, *SB = stage_words(ga, na, gb, nb, w, stg, lane), *SO = stg + WARP_MERGE_MAX;
     const uint32_t tot = na + nb, L = (tot + 31) >> 5;
     const uint32_t d = min(lane * L, tot), dend = min(d + L, tot);
     uint32_t lo = d > nb ? d - nb : 0, hi = min(d, na);
@@ -830,11 +852,22 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
             card = lc;
         }
     }
-    // warp-sized array merges, one at a time
+    // warp-sized array merges, one at a time; the first words of the next
+    // pair are requested before the current one is merged
     uint32_t wq = __ballot_sync(FULL, mode == M_WARP_ARR);
+    auto pre = [&](int k) -> WPre {
+        return prefetch_words(reinterpret_cast<const uint16_t *>(__shfl_sync(FULL, (unsigned long long)ca.p, k)),
+                              __shfl_sync(FULL, ca.card, k),
+                              reinterpret_cast<const uint16_t *>(__shfl_sync(FULL, (unsigned long long)cb.p, k)),
+                              __shfl_sync(FULL, cb.card, k), lane);
+    };
+    WPre w_cur = {0u, 0u};
+    if (wq) w_cur = pre(__ffs(wq) - 1);
     while (wq) {
         const int src = __ffs(wq) - 1;
         wq &= wq - 1;
+        WPre w_next = {0u, 0u};
+        if (wq) w_next = pre(__ffs(wq) - 1);
         const uint32_t tbl_s = __shfl_sync(FULL, tbl, src);
         const uint64_t off_s = __shfl_sync(FULL, count ? ALLOC_FAIL : off, src);
         const unsigned long long pa_s = __shfl_sync(FULL, (unsigned long long)ca.p, src);
@@ -844,10 +877,11 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
         uint64_t dsc = DESC_EMPTY;
         if (__shfl_sync(FULL, (uint32_t)count, src))
             c = warp_count_arrays(reinterpret_cast<const uint16_t *>(pa_s), na_s,
-                                  reinterpret_cast<const uint16_t *>(pb_s), nb_s, stg, lane);
+                                  reinterpret_cast<const uint16_t *>(pb_s), nb_s, w_cur, stg, lane);
         else
             dsc = warp_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s), na_s,
-                                    reinterpret_cast<const uint16_t *>(pb_s), nb_s, stg, lane, off_s, c);
+                                    reinterpret_cast<const uint16_t *>(pb_s), nb_s, w_cur, stg, lane, off_s, c);
+        w_cur = w_next;
         if (lane == (uint32_t)src) {
             desc = dsc;
             card = c;
@@ -867,7 +901,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     }
     if (has) {
         bytes_acc += in_payload_bytes(it.da) + in_payload_bytes(it.db);
-        if (desc != DESC_EMPTY) bytes_acc += payload_bytes(d_type(desc), d_card(desc), d_runs(desc)) + 10;
+        if (desc != DESC_EMPTY) bytes_acc += payload_bytes(d_type(desc), d_card(desc), d_runs(desc)) + META_BYTES;
     }
 }
 
@@ -1113,7 +1147,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
                 atomicAdd(&S->card, (unsigned long long)c);
                 if (ty == T_BITSET) atomicAdd(&S->nbits, 1u);
                 else atomicAdd(&S->words, (unsigned long long)word_alloc_bytes(ty, c, r));
-                ib += payload_bytes(ty, c, r) + 10;
+                ib += payload_bytes(ty, c, r) + META_BYTES;
             }
             hbytes += ib;
         }
@@ -1208,6 +1242,7 @@ struct rb_plan {
     rb_schedule gsched = {0, 0, 0, 0, 0};
     double last_ms = 0, last_lean_ms = 0, last_heavy_ms = 0;
     uint64_t last_alg = 0, last_out = 0, last_lean_bytes = 0, last_heavy_bytes = 0, last_deferred = 0;
+    uint64_t meta_bytes = 0;   // algorithmic key + metadata bytes of the inputs (and count results)
     cudaStream_t alloc_stream = nullptr;
 };
 
@@ -1257,6 +1292,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     p->pairs.resize(nq);
     std::vector<unsigned long long> tb(nq + 1);
     uint64_t npos = 0, tiles = 0, ew = 0, eb = 0, bw = 0, bb = 0, ed = 0;
+    p->meta_bytes = 0;
     for (uint64_t i = 0; i < nq; i++) {
         const rb_query &x = q[i];
         if (x.op > 3 || x.a >= pool_n || x.b >= pool_n) {
@@ -1278,6 +1314,8 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
         else if (!count && x.op == OP_ANDNOT) merge = !(nb * 8 < na || na * 8 < nb);
         else merge = mx <= 8 * mn;
         d.flags = (count ? F_COUNT : 0) | (merge ? F_MERGE : 0);
+        // the key arrays and metadata of both inputs, and a count-only result
+        p->meta_bytes += META_BYTES * (na + nb) + (count ? COUNT_BYTES : 0);
         uint64_t ns, np;
         if (merge) ns = na + nb;
         else if (count || x.op == OP_AND) ns = mn;
@@ -1521,7 +1559,7 @@ rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool
         p->defer_cap = std::max<uint64_t>(h.defer_n, 1);
         p->exact = true;
     }
-    p->last_lean_bytes = h.lean_bytes;
+    p->last_lean_bytes = h.lean_bytes + p->meta_bytes;
     p->last_heavy_bytes = h.heavy_bytes;
     p->last_deferred = h.defer_n;
     *arena = a;
@@ -1575,7 +1613,7 @@ rb_status plan_execute(rb_plan *p, rb_t **outs, uint64_t *counts, cudaStream_t s
             outs[i] = h;
         }
     }
-    p->last_alg = alg + p->h_es->lean_bytes + p->h_es->heavy_bytes;
+    p->last_alg = alg + p->h_es->lean_bytes + p->meta_bytes + p->h_es->heavy_bytes;
     p->last_out = outb;
     arena_unref(a);
     return RB_OK;
