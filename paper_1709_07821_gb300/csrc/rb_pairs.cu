@@ -356,8 +356,12 @@ __device__ __forceinline__ void prefetch_payload(const uint8_t *p, uint32_t byte
     for (uint32_t i = 0; i < n; i++) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 128 * i));
 }
 
-enum : uint32_t { M_NONE = 0, M_LANE_ARR, M_LANE_SWEEP, M_COPY, M_WARP_ARR, M_DEFER };
+enum : uint32_t { M_NONE = 0, M_LANE_ARR, M_LANE_SWEEP, M_COPY, M_WARP_ARR, M_DEFER, M_GRP_ARR };
 constexpr uint32_t WARP_MERGE_MAX = 1024;   // values of both arrays the warp merges through shared memory
+// array pairs merged GPER at a time by groups of GW lanes, each group staging
+// in a GSEG-element region (at most GRP_MAX values, so that whole words fit)
+constexpr uint32_t GW = 8, GSEG = 256, GPER = 32 / GW;
+constexpr uint32_t GRP_MAX = GSEG - 2;
 constexpr uint32_t RUN_SWEEP_MAX = 512;     // intervals one lane sweeps when runs are involved
 constexpr uint32_t QCAP = 64;               // container pairs queued per warp
 
@@ -580,7 +584,10 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
         const uint32_t ta = d_type(da), tb = d_type(db);
         if (ta == T_ARRAY && tb == T_ARRAY) {
             const uint32_t n = d_card(da) + d_card(db);
-            mode = n <= P.small_iv ? M_LANE_ARR : n <= WARP_MERGE_MAX - 2 ? M_WARP_ARR : M_DEFER;
+            mode = n <= P.small_iv ? M_LANE_ARR
+                   : n <= GRP_MAX        ? M_GRP_ARR
+                   : n <= WARP_MERGE_MAX - 2 ? M_WARP_ARR
+                                             : M_DEFER;
         } else if (ta != T_BITSET && tb != T_BITSET && n_intervals(da) + n_intervals(db) <= RUN_SWEEP_MAX) {
             mode = M_LANE_SWEEP;
         } else {
@@ -777,6 +784,243 @@ __device__ __noinline__ uint64_t warp_merge_arrays(ExecState *es, uint32_t tbl, 
     return desc;
 }
 
+// ------------------------------------------------------------ group merges
+// Array pairs of at most GRP_MAX values are merged four at a time, each by a
+// group of GW = 8 lanes, with the same steps as the warp merge above (staged
+// inputs, merge-path chunks, scans over the group, canonical encoding).  A
+// group's staging region is GSEG elements of the warp's first half of stg,
+// its output region the same stretch of the second half.  Every lane of the
+// warp runs these functions (idle groups with na = nb = 0); the shuffles sit
+// outside the loops whose trip counts differ between groups.
+
+__device__ __forceinline__ uint32_t g_incl(uint32_t x, uint32_t sl) {
+#pragma unroll
+    for (uint32_t d = 1; d < GW; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, d, GW);
+        if (sl >= d) x += y;
+    }
+    return x;
+}
+__device__ __forceinline__ uint32_t g_sum(uint32_t x) {
+#pragma unroll
+    for (uint32_t d = GW / 2; d; d >>= 1) x += __shfl_xor_sync(FULL, x, d, GW);
+    return x;
+}
+
+// both arrays of a group's pair, a then b as whole words (b starts at element
+// 2 * ceil(na / 2)); 16 loads per lane in flight, the rest (more than 128
+// words, na + nb > 254) by a second loop
+__device__ __forceinline__ uint16_t *g_stage(const uint16_t *ga, uint32_t na, const uint16_t *gb, uint32_t nb,
+                                             uint16_t *S, uint32_t sl) {
+    const uint32_t wa = (na + 1) / 2, wt = wa + (nb + 1) / 2;
+    const uint32_t *A32 = reinterpret_cast<const uint32_t *>(ga), *B32 = reinterpret_cast<const uint32_t *>(gb);
+    uint32_t *S32 = reinterpret_cast<uint32_t *>(S);
+    uint32_t v[16];
+#pragma unroll
+    for (uint32_t k = 0; k < 16; k++) {
+        const uint32_t x = k * GW + sl;
+        v[k] = x < wt ? __ldg(x < wa ? A32 + x : B32 + (x - wa)) : 0u;
+    }
+#pragma unroll
+    for (uint32_t k = 0; k < 16; k++) {
+        const uint32_t x = k * GW + sl;
+        if (x < wt) S32[x] = v[k];
+    }
+#pragma unroll 1
+    for (uint32_t x = 16 * GW + sl; x < wt; x += GW) S32[x] = __ldg(x < wa ? A32 + x : B32 + (x - wa));
+    __syncwarp();
+    return S + 2 * wa;
+}
+
+// the merge-path split of a group lane's chunk: its first element d, its end,
+// and how many of a's values precede d
+struct GChunk {
+    uint32_t d, dend, i0;
+};
+__device__ __forceinline__ GChunk g_chunk(const uint16_t *SA, uint32_t na, const uint16_t *SB, uint32_t nb,
+                                          uint32_t sl) {
+    const uint32_t tot = na + nb, L = (tot + GW - 1) / GW;
+    GChunk g;
+    g.d = min(sl * L, tot);
+    g.dend = min(g.d + L, tot);
+    uint32_t lo = g.d > nb ? g.d - nb : 0, hi = min(g.d, na);
+#pragma unroll 1
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (SA[m] <= SB[g.d - 1 - m]) lo = m + 1;
+        else hi = m;
+    }
+    g.i0 = lo;
+    return g;
+}
+
+// a op b for a group's pair (na + nb <= GRP_MAX) into the reserved output
+// off (ALLOC_FAIL: nothing written); returns the descriptor on every lane of
+// the group, card gets the cardinality
+__device__ __noinline__ uint64_t group_merge_arrays(ExecState *es, uint32_t tbl, const uint16_t *ga, uint32_t na,
+                                                    const uint16_t *gb, uint32_t nb, uint16_t *SI, uint16_t *SO,
+                                                    uint32_t sl, uint64_t off, uint32_t &card) {
+    const uint16_t *SA = SI, *SB = g_stage(ga, na, gb, nb, SI, sl);
+    const GChunk g = g_chunk(SA, na, SB, nb, sl);
+    uint32_t i = g.i0, j = g.d - g.i0, pa = g.i0 > 0 ? (uint32_t)SA[g.i0 - 1] : 0xFFFFFFFFu;
+    uint32_t take_a = 0, kept = 0, c = 0, r = 0, first = 0, last = 0xFFFFFFFEu;
+#pragma unroll 1
+    for (uint32_t s = 0; g.d + s < g.dend; s++) {
+        const uint32_t va = i < na ? (uint32_t)SA[i] : KEY_END, vb = j < nb ? (uint32_t)SB[j] : KEY_END;
+        const bool ta = va <= vb;
+        const uint32_t v = ta ? va : vb;
+        const bool ino = ta ? (vb == va) : (pa == vb);
+        take_a |= (uint32_t)ta << s;
+        if ((tbl >> ((ta ? 2u : 0u) | (ino ? 1u : 0u))) & 1u) {
+            kept |= 1u << s;
+            if (c == 0) first = v;
+            r += (v != last + 1);
+            last = v;
+            c++;
+        }
+        pa = ta ? va : pa;
+        i += ta;
+        j += !ta;
+    }
+    // a lane's first kept value continues a run when it follows the last kept
+    // value of the group's lanes before it (a max-scan finds that value)
+    uint32_t m = c ? last + 1 : 0;
+#pragma unroll
+    for (uint32_t dd = 1; dd < GW; dd <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, m, dd, GW);
+        if (sl >= dd) m = max(m, y);
+    }
+    uint32_t prev = __shfl_up_sync(FULL, m, 1, GW);
+    if (sl == 0) prev = 0;
+    if (c && prev != 0 && first == prev) r--;
+    const uint32_t cincl = g_incl(c, sl), rincl = g_incl(r, sl);
+    const uint32_t C = __shfl_sync(FULL, cincl, GW - 1, GW), R = __shfl_sync(FULL, rincl, GW - 1, GW);
+    card = C;
+    const bool emit = off != ALLOC_FAIL && C != 0;
+    const uint32_t ty = canon_type(C, R);   // C <= GRP_MAX: array or runs
+    if (emit) {
+        uint32_t qq = cincl - c;
+        i = g.i0;
+        j = g.d - g.i0;
+#pragma unroll 1
+        for (uint32_t s = 0; g.d + s < g.dend; s++) {
+            const bool ta = (take_a >> s) & 1u;
+            const uint16_t v = ta ? SA[i] : SB[j];
+            i += ta;
+            j += !ta;
+            if ((kept >> s) & 1u) SO[qq++] = v;
+        }
+    }
+    __syncwarp();
+    if (emit && ty == T_RUN) {
+        // run starts of this lane's kept values, indexed by run, into the
+        // (no longer needed) staging region
+        uint32_t q0 = cincl - c, k = rincl - r;
+#pragma unroll 1
+        for (uint32_t x = q0; x < q0 + c; x++)
+            if (x == 0 || (uint32_t)SO[x] != (uint32_t)SO[x - 1] + 1) SI[k++] = (uint16_t)x;
+    }
+    __syncwarp();
+    uint64_t desc = DESC_EMPTY;
+    if (emit) {
+        if (ty == T_ARRAY) {
+            uint16_t *out = reinterpret_cast<uint16_t *>(es->arena + off);
+#pragma unroll 1
+            for (uint32_t x = sl; x < C; x += GW) out[x] = SO[x];
+        } else {
+            uint32_t *out = reinterpret_cast<uint32_t *>(es->arena + off);
+#pragma unroll 1
+            for (uint32_t x = sl; x < R; x += GW) {
+                const uint32_t s = SI[x], e = (x + 1 < R ? (uint32_t)SI[x + 1] : C) - 1;
+                out[x] = (uint32_t)SO[s] | ((uint32_t)(SO[e] - SO[s]) << 16);
+            }
+        }
+        desc = mk_desc(C, ty, ty == T_RUN ? R : 0, off);
+    }
+    __syncwarp();
+    return desc;
+}
+
+// |a n b| for a group's pair (na + nb <= GRP_MAX), on every lane of the group
+__device__ __noinline__ uint32_t group_count_arrays(const uint16_t *ga, uint32_t na, const uint16_t *gb, uint32_t nb,
+                                                    uint16_t *SI, uint32_t sl) {
+    const uint16_t *SA = SI, *SB = g_stage(ga, na, gb, nb, SI, sl);
+    const GChunk g = g_chunk(SA, na, SB, nb, sl);
+    uint32_t i = g.i0, j = g.d - g.i0, c = 0;
+#pragma unroll 1
+    for (uint32_t s = g.d; s < g.dend; s++) {
+        const uint32_t va = i < na ? (uint32_t)SA[i] : KEY_END, vb = j < nb ? (uint32_t)SB[j] : KEY_END;
+        const bool ta = va <= vb;
+        c += ta && va == vb;
+        i += ta;
+        j += !ta;
+    }
+    const uint32_t C = g_sum(c);
+    __syncwarp();
+    return C;
+}
+
+// Group-sized array merges of the lanes in gq, GPER at a time: group g of
+// lanes takes the g-th of the next GPER queued pairs; each served lane gets
+// its pair's descriptor and cardinality
+__device__ __noinline__ void process_groups(ExecState *es, uint32_t gq, const CRef &ca, const CRef &cb, uint32_t tbl,
+                                            uint64_t off, bool count, uint16_t *stg, uint32_t lane, uint64_t &desc,
+                                            uint32_t &card) {
+    const uint32_t g = lane / GW, sl = lane % GW;
+    uint16_t *GI = stg + GSEG * g, *GO = stg + WARP_MERGE_MAX + GSEG * g;
+#pragma unroll 1
+    while (gq) {
+        // the (up to) GPER queued lanes served now; group g takes the
+        // g-th of them
+        uint32_t rest = gq;
+#pragma unroll
+        for (uint32_t x = 0; x < GPER; x++) rest &= rest - 1;
+        const uint32_t taken = gq & ~rest;
+        gq = rest;
+        uint32_t mine_g = taken;
+        for (uint32_t x = 0; x < g; x++) mine_g &= mine_g - 1;
+        const uint32_t src = mine_g ? (uint32_t)__ffs(mine_g) - 1 : 32u;
+        const uint32_t s = src < 32 ? src : 0;
+        const unsigned long long pa_s = __shfl_sync(FULL, (unsigned long long)ca.p, s);
+        const unsigned long long pb_s = __shfl_sync(FULL, (unsigned long long)cb.p, s);
+        uint32_t na_s = __shfl_sync(FULL, ca.card, s), nb_s = __shfl_sync(FULL, cb.card, s);
+        const uint32_t tbl_s = __shfl_sync(FULL, tbl, s);
+        const uint64_t off_s = __shfl_sync(FULL, count ? ALLOC_FAIL : off, s);
+        const bool cnt_s = __shfl_sync(FULL, (uint32_t)count, s) != 0;
+        if (src == 32) na_s = nb_s = 0;
+        uint32_t c = 0;
+        uint64_t dsc = DESC_EMPTY;
+        // count-only and materialising queries may share a batch: both
+        // functions run on every lane, each group uses its own result
+        const bool any_cnt = __any_sync(FULL, src < 32 && cnt_s);
+        const bool any_mat = __any_sync(FULL, src < 32 && !cnt_s);
+        if (any_cnt) {
+            const uint32_t cc = group_count_arrays(reinterpret_cast<const uint16_t *>(pa_s), cnt_s ? na_s : 0,
+                                                   reinterpret_cast<const uint16_t *>(pb_s), cnt_s ? nb_s : 0, GI,
+                                                   sl);
+            if (cnt_s) c = cc;
+        }
+        if (any_mat) {
+            uint32_t cm = 0;
+            const uint64_t dm = group_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s),
+                                                   cnt_s ? 0 : na_s, reinterpret_cast<const uint16_t *>(pb_s),
+                                                   cnt_s ? 0 : nb_s, GI, GO, sl, off_s, cm);
+            if (!cnt_s) {
+                c = cm;
+                dsc = dm;
+            }
+        }
+        // each served lane reads its group's result from the group's first lane
+        const uint32_t mine = (taken >> lane) & 1u ? __popc(taken & lanemask_lt(lane)) : 0u;
+        const uint32_t c_r = __shfl_sync(FULL, c, mine * GW);
+        const uint64_t d_r = __shfl_sync(FULL, dsc, mine * GW);
+        if ((taken >> lane) & 1u) {
+            desc = d_r;
+            card = c_r;
+        }
+    }
+}
+
 // Process n <= 32 queued container pairs, one per lane (warp-sized ones by
 // the whole warp in turn), with one allocation for all their outputs.  The
 // queue holds pairs only: copies are done during the key merge.
@@ -800,7 +1044,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     // sizes: exact for run sweeps, the array bound for array merges
     uint32_t bytes = 0, lc = 0, lr = 0, lt = 0;
     if (!count) {
-        if (mode == M_LANE_ARR || mode == M_WARP_ARR) {
+        if (mode == M_LANE_ARR || mode == M_WARP_ARR || mode == M_GRP_ARR) {
             bytes = array_result_bound(op, ca.card, cb.card);
         } else if (mode == M_LANE_SWEEP) {
             lane_sweep<false>(op, iv_src(ca), iv_src(cb), lc, lr, 0, nullptr);
@@ -852,6 +1096,9 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
             card = lc;
         }
     }
+    // group-sized array merges, GPER at a time
+    const uint32_t gq = __ballot_sync(FULL, mode == M_GRP_ARR);
+    if (gq) process_groups(es, gq, ca, cb, tbl, off, count, stg, lane, desc, card);
     // warp-sized array merges, one at a time; the first words of the next
     // pair are requested before the current one is merged
     uint32_t wq = __ballot_sync(FULL, mode == M_WARP_ARR);
