@@ -244,18 +244,375 @@ __device__ void multi_tile(const MParams &P, unsigned long long t, uint64_t *T0,
     }
 }
 
+// ------------------------------------------------------------ fast path
+// Queries of at most MK members take this path.  A tile is 32 consecutive
+// output keys (AND: keys of the member with the fewest keys; OR: ranks in the
+// query's key union, read back from its presence bitmap).  Each member's
+// containers for those keys are located once per tile: one binary search per
+// member for the key range the tile spans, then a coalesced scan of that
+// range (or, when a member holds many more keys there, a binary search per
+// output key).  A key whose containers are all arrays with at most LCAP
+// values in play is then merged by its own lane (OR: successive merges of
+// the sorted arrays; AND: the smallest array filtered by binary search in
+// the others), in lane-private columns of the two tiles; the other keys are
+// folded by the whole warp in the tiles, as the general path does.
+constexpr uint32_t MK = 8;
+constexpr uint32_t LCAP = 128;   // 4096 u16 per tile / 32 lanes
+constexpr uint32_t NOIX = 0xFFFFFFFFu;
+constexpr uint32_t MKEY_END = 0x10000u;
+
+struct MScratch {
+    uint32_t ix[MK][32];       // container of output key `lane` in member i (NOIX: none)
+    uint32_t keys[32];         // the tile's output keys (MKEY_END past the last)
+    uint32_t lo[MK], hi[MK];   // each member's keys within the tile's key range
+};
+constexpr uint32_t WARP_SMEM = 16384 + sizeof(MScratch);
+
+// index of the n-th (from 0) set bit of x, n < popcount(x)
+__device__ __forceinline__ uint32_t nth_set_bit(uint64_t x, uint32_t n) {
+    uint32_t b = 0;
+#pragma unroll
+    for (uint32_t w = 32; w; w >>= 1) {
+        const uint32_t lo = __popcll(x & ((1ull << w) - 1ull));
+        if (n >= lo) {
+            n -= lo;
+            x >>= w;
+            b += w;
+        }
+    }
+    return b;
+}
+
+// element e of a lane's column in a tile used as 4096 u16 (conflict-light:
+// consecutive lanes share 4-byte words)
+__device__ __forceinline__ uint16_t &col(uint64_t *T, uint32_t e, uint32_t lane) {
+    return reinterpret_cast<uint16_t *>(T)[e * 32 + lane];
+}
+
+// first index in sorted a[0..n) holding a value >= v
+__device__ __forceinline__ uint32_t lower_bound_u16(const uint16_t *a, uint32_t n, uint32_t v) {
+    uint32_t lo = 0, hi = n;
+#pragma unroll 1
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if ((uint32_t)__ldg(a + m) < v) lo = m + 1;
+        else hi = m;
+    }
+    return lo;
+}
+
+// count c, runs r and canonical encoding of a lane's column X[0..n); writes
+// the container at out (4-byte aligned; arrays in whole words) when out != 0
+__device__ __forceinline__ uint32_t col_runs(uint64_t *X, uint32_t n, uint32_t lane) {
+    uint32_t r = 0, last = 0xFFFFFFFEu;
+#pragma unroll 1
+    for (uint32_t e = 0; e < n; e++) {
+        const uint32_t v = col(X, e, lane);
+        r += (v != last + 1);
+        last = v;
+    }
+    return r;
+}
+__device__ __forceinline__ void col_emit(uint64_t *X, uint32_t n, uint32_t ty, uint8_t *out, uint32_t lane) {
+    if (ty == T_ARRAY) {
+        uint32_t *o = reinterpret_cast<uint32_t *>(out);
+#pragma unroll 1
+        for (uint32_t e = 0; e < n; e += 2)
+            o[e / 2] = (uint32_t)col(X, e, lane) | (e + 1 < n ? (uint32_t)col(X, e + 1, lane) << 16 : 0u);
+    } else {
+        uint32_t *o = reinterpret_cast<uint32_t *>(out);
+        uint32_t k = 0, s = col(X, 0, lane), last = s;
+#pragma unroll 1
+        for (uint32_t e = 1; e < n; e++) {
+            const uint32_t v = col(X, e, lane);
+            if (v != last + 1) {
+                o[k++] = s | ((last - s) << 16);
+                s = v;
+            }
+            last = v;
+        }
+        o[k] = s | ((last - s) << 16);
+    }
+}
+
+// after the warp folded one key into T0: count, canonical type, emit, record
+__device__ void emit_folded(MState *es, const MultiDev &qd, uint64_t *T0, uint64_t *T1, uint32_t key, uint32_t pos,
+                            unsigned long long &card_acc, unsigned long long &words_acc, uint32_t &bits_acc,
+                            uint32_t lane) {
+    uint32_t c, r;
+    t_combine<false>(nullptr, T0, T0, OP_OR, c, r, lane);
+    __syncwarp();
+    if (qd.count_only) {
+        if (lane == 0) card_acc += c;
+        return;
+    }
+    uint64_t desc = DESC_EMPTY;
+    if (c) {
+        const uint32_t ty = canon_type(c, r);
+        if (ty == T_BITSET) {
+            const uint64_t off = alloc_b(es, lane);
+            if (off != ALLOC_FAIL) {
+                t_emit_bitset(T0, reinterpret_cast<uint64_t *>(es->arena + off), lane);
+                desc = mk_desc(c, ty, 0, off);
+            }
+        } else {
+            const uint32_t bytes = word_alloc_bytes(ty, c, r);
+            const uint64_t off = alloc_w(es, bytes, lane);
+            if (off != ALLOC_FAIL) {
+                if (ty == T_ARRAY) {
+                    t_emit_array(T0, reinterpret_cast<uint16_t *>(es->arena + off), lane);
+                } else {
+                    uint16_t *S = reinterpret_cast<uint16_t *>(T1);
+                    t_emit_runs(T0, S, S + 2048, reinterpret_cast<uint32_t *>(es->arena + off), r, lane);
+                }
+                desc = mk_desc(c, ty, ty == T_RUN ? r : 0, off);
+            }
+        }
+    }
+    if (lane == 0) {
+        es->descs[qd.slot_base + pos] = desc;
+        es->keys[qd.slot_base + pos] = (uint16_t)key;
+        if (desc != DESC_EMPTY) {
+            card_acc += c;
+            if (d_type(desc) == T_BITSET) bits_acc++;
+            else words_acc += word_alloc_bytes(d_type(desc), c, r);
+        }
+    }
+    __syncwarp();
+}
+
+__device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd, uint32_t local, uint64_t *T0,
+                                uint64_t *T1, MScratch *MS, uint32_t lane) {
+    const uint32_t *mem = P.members + qd.mbase;
+    const uint32_t k = qd.k;
+    const uint32_t p0 = local * 32u;
+    uint32_t n_act, key = MKEY_END, pos = 0;
+    if (qd.op == OP_AND) {
+        n_act = p0 < qd.n_slots ? min(32u, qd.n_slots - p0) : 0u;
+        if (lane < n_act) {
+            key = __ldg(P.pool[mem[qd.driver]].keys + p0 + lane);
+            pos = p0 + lane;
+        }
+    } else {
+        const uint32_t npos = P.stats[q].n_pos;   // written by k_rank
+        n_act = p0 < npos ? min(32u, npos - p0) : 0u;
+        if (lane < n_act) {
+            pos = p0 + lane;
+            const uint32_t *pf = P.prefix + (size_t)qd.pres_idx * 1024;
+            uint32_t lo = 0, hi = 1024;   // the last word whose prefix is <= pos
+#pragma unroll 1
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (pf[mid] <= pos) lo = mid;
+                else hi = mid;
+            }
+            key = lo * 64 + nth_set_bit(P.pres[(size_t)qd.pres_idx * 1024 + lo], pos - pf[lo]);
+        }
+    }
+    if (n_act == 0) return;
+    MS->keys[lane] = key;
+    __syncwarp();
+    const uint32_t k_lo = MS->keys[0], k_hi = MS->keys[n_act - 1];
+    if (lane < k) {
+        const BmView V = P.pool[mem[lane]];
+        const uint32_t lo = lower_bound16(V.keys, V.n, k_lo);
+        MS->lo[lane] = lo;
+        MS->hi[lane] = lo + lower_bound16(V.keys + lo, V.n - lo, k_hi + 1);
+    }
+    for (uint32_t i = 0; i < k; i++) MS->ix[i][lane] = NOIX;
+    __syncwarp();
+    // locate every member's container of each output key
+#pragma unroll 1
+    for (uint32_t i = 0; i < k; i++) {
+        const BmView V = P.pool[mem[i]];
+        const uint32_t lo = MS->lo[i], hi = MS->hi[i];
+        if (hi - lo <= 64) {
+#pragma unroll 1
+            for (uint32_t x0 = lo; x0 < hi; x0 += 32) {
+                const uint32_t x = x0 + lane;
+                if (x < hi) {
+                    const uint32_t kk = __ldg(V.keys + x);
+                    uint32_t a = 0, b = n_act;   // first output key >= kk
+#pragma unroll 1
+                    while (a < b) {
+                        const uint32_t m = (a + b) >> 1;
+                        if (MS->keys[m] < kk) a = m + 1;
+                        else b = m;
+                    }
+                    if (a < n_act && MS->keys[a] == kk) MS->ix[i][a] = x;
+                }
+            }
+        } else if (lane < n_act) {
+            const uint32_t j = lo + lower_bound16(V.keys + lo, hi - lo, key);
+            if (j < hi && __ldg(V.keys + j) == key) MS->ix[i][lane] = j;
+        }
+    }
+    __syncwarp();
+    // what each output key needs
+    MState *es = P.es;
+    const bool is_and = qd.op == OP_AND;
+    uint32_t present = 0, sum_card = 0, min_card = 0xFFFFFFFFu, min_i = 0;
+    bool all_arr = true;
+    unsigned long long in_acc = 0;
+    if (lane < n_act) {
+        for (uint32_t i = 0; i < k; i++) {
+            const uint32_t j = MS->ix[i][lane];
+            if (j == NOIX) continue;
+            const uint64_t d = __ldg(P.pool[mem[i]].descs + j);
+            present++;
+            sum_card += d_card(d);
+            if (d_card(d) < min_card) { min_card = d_card(d); min_i = i; }
+            all_arr = all_arr && d_type(d) == T_ARRAY;
+            in_acc += in_payload_bytes(d) + 15;
+        }
+    }
+    const bool empty = lane < n_act && is_and && present < k;
+    const bool lane_path = lane < n_act && !empty && all_arr && (is_and ? min_card <= LCAP : sum_card <= LCAP);
+    const bool warp_path = lane < n_act && !empty && !lane_path;
+    if (empty && !qd.count_only) {
+        es->descs[qd.slot_base + pos] = DESC_EMPTY;
+        es->keys[qd.slot_base + pos] = (uint16_t)key;
+    }
+    if (empty) in_acc = 0;   // an absent container ends the key's AND: nothing is read
+    // lane path: the key's result in the lane's column of T0 or T1
+    uint64_t *X = T0, *Y = T1;
+    uint32_t n = 0;
+    if (lane_path) {
+        if (is_and) {
+            const BmView V0 = P.pool[mem[min_i]];
+            const uint64_t d0 = __ldg(V0.descs + MS->ix[min_i][lane]);
+            const uint16_t *A0 = reinterpret_cast<const uint16_t *>(V0.base + d_off(d0));
+            n = d_card(d0);
+            for (uint32_t e = 0; e < n; e++) col(X, e, lane) = __ldg(A0 + e);
+            for (uint32_t i = 0; i < k && n; i++) {
+                if (i == min_i) continue;
+                const BmView V = P.pool[mem[i]];
+                const uint64_t d = __ldg(V.descs + MS->ix[i][lane]);
+                const uint16_t *A = reinterpret_cast<const uint16_t *>(V.base + d_off(d));
+                const uint32_t na = d_card(d);
+                uint32_t m = 0, from = 0;
+                for (uint32_t e = 0; e < n; e++) {
+                    const uint32_t v = col(X, e, lane);
+                    from += lower_bound_u16(A + from, na - from, v);
+                    if (from < na && __ldg(A + from) == v) col(X, m++, lane) = (uint16_t)v;
+                }
+                n = m;
+            }
+        } else {
+            for (uint32_t i = 0; i < k; i++) {
+                const uint32_t j = MS->ix[i][lane];
+                if (j == NOIX) continue;
+                const BmView V = P.pool[mem[i]];
+                const uint64_t d = __ldg(V.descs + j);
+                const uint16_t *A = reinterpret_cast<const uint16_t *>(V.base + d_off(d));
+                const uint32_t na = d_card(d);
+                // Y = X u A, both sorted, duplicates once
+                uint32_t x = 0, y = 0, m = 0;
+                while (x < n || y < na) {
+                    const uint32_t vx = x < n ? (uint32_t)col(X, x, lane) : MKEY_END;
+                    const uint32_t va = y < na ? (uint32_t)__ldg(A + y) : MKEY_END;
+                    const uint32_t v = vx < va ? vx : va;
+                    col(Y, m++, lane) = (uint16_t)v;
+                    x += vx == v;
+                    y += va == v;
+                }
+                n = m;
+                uint64_t *t = X;
+                X = Y;
+                Y = t;
+            }
+        }
+    }
+    uint32_t r = 0, ty = T_ARRAY, bytes = 0;
+    if (lane_path && n) {
+        r = col_runs(X, n, lane);
+        ty = canon_type(n, r);   // n <= LCAP: array or runs
+        if (!qd.count_only) bytes = word_alloc_bytes(ty, n, r);
+    }
+    unsigned long long card_acc = lane_path ? n : 0, words_acc = bytes;
+    uint32_t bits_acc = 0;
+    if (!qd.count_only) {
+        const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
+        uint64_t base = ALLOC_FAIL;
+        if (total) base = alloc_w(es, total, lane);
+        if (lane_path) {
+            uint64_t desc = DESC_EMPTY;
+            if (n && base != ALLOC_FAIL) {
+                const uint64_t off = base + incl - bytes;
+                col_emit(X, n, ty, es->arena + off, lane);
+                desc = mk_desc(n, ty, ty == T_RUN ? r : 0, off);
+            } else {
+                card_acc = 0;
+                words_acc = 0;
+            }
+            es->descs[qd.slot_base + pos] = desc;
+            es->keys[qd.slot_base + pos] = (uint16_t)key;
+        }
+    }
+    __syncwarp();
+    // warp path: one key at a time in the tiles
+    uint32_t wl = __ballot_sync(FULL, warp_path);
+    while (wl) {
+        const int src = __ffs(wl) - 1;
+        wl &= wl - 1;
+        const uint32_t k_key = __shfl_sync(FULL, key, src), k_pos = __shfl_sync(FULL, pos, src);
+        const uint32_t k_min = __shfl_sync(FULL, min_i, src);
+        if (is_and) {
+            const BmView D = P.pool[mem[k_min]];
+            t_decode(T0, cref(D.base, __ldg(D.descs + MS->ix[k_min][src])), lane);
+            for (uint32_t i = 0; i < k; i++) {
+                if (i == k_min) continue;
+                const BmView V = P.pool[mem[i]];
+                fold_into(T0, T1, cref(V.base, __ldg(V.descs + MS->ix[i][src])), OP_AND, lane);
+            }
+        } else {
+            t_zero(T0, lane);
+            __syncwarp();
+            for (uint32_t i = 0; i < k; i++) {
+                const uint32_t j = MS->ix[i][src];
+                if (j == NOIX) continue;
+                const BmView V = P.pool[mem[i]];
+                fold_into(T0, T1, cref(V.base, __ldg(V.descs + j)), OP_OR, lane);
+            }
+        }
+        emit_folded(es, qd, T0, T1, k_key, k_pos, card_acc, words_acc, bits_acc, lane);
+    }
+    // per-query sums
+    card_acc = warp_sum64(card_acc);
+    words_acc = warp_sum64(words_acc);
+    in_acc = warp_sum64(in_acc);
+    bits_acc = warp_sum(bits_acc);
+    if (lane == 0) {
+        MStats *S = P.stats + q;
+        if (card_acc) atomicAdd(&S->card, card_acc);
+        if (words_acc) atomicAdd(&S->words, words_acc);
+        if (bits_acc) atomicAdd(&S->nbits, bits_acc);
+        if (in_acc) atomicAdd(&S->in_bytes, in_acc);
+    }
+    __syncwarp();
+}
+
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) k_multi(MParams P) {
     extern __shared__ __align__(16) uint64_t smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t *T0 = smem + (size_t)warp * 2048;
+    uint64_t *T0 = smem + (size_t)warp * (WARP_SMEM / 8);
     uint64_t *T1 = T0 + 1024;
+    MScratch *MS = reinterpret_cast<MScratch *>(T0 + 2048);
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(&P.es->work, 1ull);
         t = __shfl_sync(FULL, t, 0);
         if (t >= P.n_tiles) break;
-        multi_tile(P, t, T0, T1, lane);
+        uint32_t lo = 0, hi = P.n_q;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (P.tile_base[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        const MultiDev qd = P.qs[lo];
+        if (qd.k <= MK) multi_tile_fast(P, lo, qd, (uint32_t)(t - P.tile_base[lo]), T0, T1, MS, lane);
+        else multi_tile(P, t, T0, T1, lane);
     }
 }
 
@@ -537,7 +894,7 @@ rb_status multi_prepare(const rb *const *pool, const BmView *d_pool, uint32_t po
 template <int W>
 static void launch_multi_w(const MParams &P, int ctas, cudaStream_t s) {
     static bool attr = false;
-    const int smem = W * 16384;
+    const int smem = W * WARP_SMEM;
     if (!attr) {
         cudaFuncSetAttribute(k_multi<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;

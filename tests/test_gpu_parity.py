@@ -238,6 +238,13 @@ def test_multi_way_mixed_types(rb, orc, workloads_mod):
     vals = [pool.values(i) for i in range(pool.n)]
     G = [rb.Bitmap.from_sorted(v) for v in vals]
     O = [orc.Bitmap.from_sorted(v) for v in vals]
-    for op in (0, 1):
-        m, card = rb.multi_op(op, G)
-        assert_layout_eq(m.layout(), orc.Bitmap.multi(op, O).layout(), f"mixed op{op}")
+    # up to 8 members take the per-tile container lookup with lane merges,
+    # more members the general path
+    for k in (2, 3, 8, 16):
+        for op in (0, 1):
+            m, card = rb.multi_op(op, G[:k])
+            exp = orc.Bitmap.multi(op, O[:k])
+            assert card == exp.card
+            assert_layout_eq(m.layout(), exp.layout(), f"mixed op{op} k{k}")
+            _, c2 = rb.multi_op(op, G[:k], count_only=True)
+            assert c2 == exp.card
