@@ -2,11 +2,12 @@
 // unions" computes the union of many sets; this engine folds the k
 // containers of each output key once, instead of a sequential fold).
 //
-// Slots.  AND: the keys of the member with the fewest keys (a key survives
-// only if every member has it).  OR: the keys of every member; a slot owns
-// its key if no earlier member has it, and the key's output position is its
-// rank among the distinct keys, read from a per-query 65536-bit presence
-// bitmap and the prefix of its word popcounts.
+// Output keys.  AND: the keys of the member with the fewest keys (a key
+// survives only if every member has it), in that member's order.  OR: the
+// distinct keys of all members in ascending order: output index p is the
+// p-th set bit of a per-query 65536-bit presence bitmap, found through the
+// prefix of its word popcounts.  Queries of up to MK members work on tiles
+// of 32 output keys (fast path below); wider ones on one key per tile.
 #include <algorithm>
 #include <cstring>
 
@@ -17,8 +18,6 @@ using namespace rbi;
 using namespace rbd;
 
 namespace {
-
-constexpr uint32_t KIND_NONE = 0, KIND_EMPTY = 1, KIND_FOLD = 2;
 
 struct MultiDev {
     uint32_t op, count_only, k, driver;
@@ -103,145 +102,6 @@ __device__ uint64_t alloc_b(MState *es, uint32_t lane) {
         return ALLOC_FAIL;
     }
     return es->bits_off + old;
-}
-
-__device__ void multi_tile(const MParams &P, unsigned long long t, uint64_t *T0, uint64_t *T1, uint32_t lane) {
-    uint32_t lo = 0, hi = P.n_q;
-    while (hi - lo > 1) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (P.tile_base[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    const uint32_t q = lo;
-    const MultiDev qd = P.qs[q];
-    const uint32_t *mem = P.members + qd.mbase;
-    const uint32_t slot = (uint32_t)(t - P.tile_base[q]) * 32u + lane;
-    uint32_t kind = KIND_NONE, key = 0, pos = 0;
-    if (slot < qd.n_slots) {
-        if (qd.op == OP_AND) {
-            const BmView D = P.pool[mem[qd.driver]];
-            key = __ldg(D.keys + slot);
-            pos = slot;
-            kind = KIND_FOLD;
-            for (uint32_t i = 0; i < qd.k; i++) {
-                if (i == qd.driver) continue;
-                uint32_t j;
-                if (!find_key(P.pool[mem[i]], key, j)) { kind = KIND_EMPTY; break; }
-            }
-        } else {
-            const uint32_t *mo = P.moff + qd.obase;
-            uint32_t l = 0, h = qd.k;   // largest i with mo[i] <= slot
-            while (h - l > 1) {
-                uint32_t m = (l + h) >> 1;
-                if (mo[m] <= slot) l = m;
-                else h = m;
-            }
-            const BmView V = P.pool[mem[l]];
-            key = __ldg(V.keys + (slot - mo[l]));
-            bool owner = true;
-            for (uint32_t i = 0; i < l && owner; i++) {
-                uint32_t j;
-                if (find_key(P.pool[mem[i]], key, j)) owner = false;
-            }
-            if (owner) {
-                kind = KIND_FOLD;
-                const unsigned long long *pr = P.pres + (size_t)qd.pres_idx * 1024;
-                const uint32_t w = key >> 6;
-                pos = P.prefix[(size_t)qd.pres_idx * 1024 + w] + __popcll(pr[w] & ((1ull << (key & 63)) - 1ull));
-            }
-        }
-    }
-    MState *es = P.es;
-    uint16_t *OKEY = es->keys + qd.slot_base;
-    uint64_t *ODESC = es->descs + qd.slot_base;
-    if (kind == KIND_EMPTY && !qd.count_only) {
-        ODESC[pos] = DESC_EMPTY;
-        OKEY[pos] = (uint16_t)key;
-    }
-    unsigned long long card_acc = 0, words_acc = 0, in_acc = 0;
-    uint32_t bits_acc = 0;
-    uint32_t lm = __ballot_sync(FULL, kind == KIND_FOLD);
-    while (lm) {
-        const int src = __ffs(lm) - 1;
-        lm &= lm - 1;
-        const uint32_t k_key = __shfl_sync(FULL, key, src), k_pos = __shfl_sync(FULL, pos, src);
-        // fold the k containers of this key
-        if (qd.op == OP_AND) {
-            const BmView D = P.pool[mem[qd.driver]];
-            uint32_t j;
-            find_key(D, k_key, j);
-            const uint64_t d0 = __ldg(D.descs + j);
-            t_decode(T0, cref(D.base, d0), lane);
-            in_acc += in_payload_bytes(d0) + 15;
-            for (uint32_t i = 0; i < qd.k; i++) {
-                if (i == qd.driver) continue;
-                const BmView V = P.pool[mem[i]];
-                find_key(V, k_key, j);
-                const uint64_t d = __ldg(V.descs + j);
-                in_acc += in_payload_bytes(d) + 15;
-                fold_into(T0, T1, cref(V.base, d), OP_AND, lane);
-            }
-        } else {
-            t_zero(T0, lane);
-            __syncwarp();
-            for (uint32_t i = 0; i < qd.k; i++) {
-                const BmView V = P.pool[mem[i]];
-                uint32_t j;
-                if (!find_key(V, k_key, j)) continue;
-                const uint64_t d = __ldg(V.descs + j);
-                in_acc += in_payload_bytes(d) + 15;
-                fold_into(T0, T1, cref(V.base, d), OP_OR, lane);
-            }
-        }
-        uint32_t c, r;
-        t_combine<false>(nullptr, T0, T0, OP_OR, c, r, lane);
-        __syncwarp();
-        if (qd.count_only) {
-            card_acc += c;
-            continue;
-        }
-        uint64_t desc = DESC_EMPTY;
-        if (c) {
-            const uint32_t ty = canon_type(c, r);
-            if (ty == T_BITSET) {
-                const uint64_t off = alloc_b(es, lane);
-                if (off != ALLOC_FAIL) {
-                    t_emit_bitset(T0, reinterpret_cast<uint64_t *>(es->arena + off), lane);
-                    desc = mk_desc(c, ty, 0, off);
-                }
-            } else {
-                const uint32_t bytes = word_alloc_bytes(ty, c, r);
-                const uint64_t off = alloc_w(es, bytes, lane);
-                if (off != ALLOC_FAIL) {
-                    if (ty == T_ARRAY) {
-                        t_emit_array(T0, reinterpret_cast<uint16_t *>(es->arena + off), lane);
-                    } else {
-                        uint16_t *S = reinterpret_cast<uint16_t *>(T1);
-                        t_emit_runs(T0, S, S + 2048, reinterpret_cast<uint32_t *>(es->arena + off), r, lane);
-                    }
-                    desc = mk_desc(c, ty, ty == T_RUN ? r : 0, off);
-                }
-            }
-        }
-        if (lane == 0) {
-            ODESC[k_pos] = desc;
-            OKEY[k_pos] = (uint16_t)k_key;
-            if (desc != DESC_EMPTY) {
-                card_acc += c;
-                if (d_type(desc) == T_BITSET) bits_acc++;
-                else words_acc += word_alloc_bytes(d_type(desc), c, r);
-            }
-        }
-        __syncwarp();
-    }
-    // per lane accumulators are only on lane 0 except in_acc/card (uniform)
-    if (lane == 0) {
-        MStats *S = P.stats + q;
-        if (card_acc) atomicAdd(&S->card, card_acc);
-        if (words_acc) atomicAdd(&S->words, words_acc);
-        if (bits_acc) atomicAdd(&S->nbits, bits_acc);
-        if (in_acc) atomicAdd(&S->in_bytes, in_acc);
-    }
 }
 
 // ------------------------------------------------------------ fast path
@@ -381,34 +241,111 @@ __device__ void emit_folded(MState *es, const MultiDev &qd, uint64_t *T0, uint64
     __syncwarp();
 }
 
+// key of output index p of query q: AND, the p-th key of the member with the
+// fewest keys; OR, the p-th key of the union (its presence bitmap and word
+// prefix were built by k_presence and k_rank).  False past the last index.
+__device__ __forceinline__ bool out_key(const MParams &P, uint32_t q, const MultiDev &qd, const uint32_t *mem,
+                                        uint32_t p, uint32_t &key) {
+    if (qd.op == OP_AND) {
+        if (p >= qd.n_slots) return false;
+        key = __ldg(P.pool[mem[qd.driver]].keys + p);
+        return true;
+    }
+    if (p >= P.stats[q].n_pos) return false;
+    const uint32_t *pf = P.prefix + (size_t)qd.pres_idx * 1024;
+    uint32_t lo = 0, hi = 1024;   // the last word whose prefix is <= p
+#pragma unroll 1
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pf[mid] <= p) lo = mid;
+        else hi = mid;
+    }
+    key = lo * 64 + nth_set_bit(P.pres[(size_t)qd.pres_idx * 1024 + lo], p - pf[lo]);
+    return true;
+}
+
+// Queries of more than MK members (wide unions and intersections): one
+// output key per tile.  The warp's lanes search the members for the key 32
+// at a time, then the key's containers are folded into T0 one after another
+// (AND: only if every member holds the key) and the result is encoded once.
+__device__ void multi_key_wide(const MParams &P, uint32_t q, const MultiDev &qd, uint32_t p, uint64_t *T0,
+                               uint64_t *T1, uint32_t lane) {
+    const uint32_t *mem = P.members + qd.mbase;
+    uint32_t key = 0;
+    if (!out_key(P, q, qd, mem, p, key)) return;
+    MState *es = P.es;
+    const bool is_and = qd.op == OP_AND;
+    if (is_and) {
+        bool absent = false;
+#pragma unroll 1
+        for (uint32_t i0 = 0; i0 < qd.k && !absent; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            uint32_t j;
+            absent = __any_sync(FULL, i < qd.k && !find_key(P.pool[mem[i]], key, j));
+        }
+        if (absent) {
+            if (!qd.count_only && lane == 0) {
+                es->descs[qd.slot_base + p] = DESC_EMPTY;
+                es->keys[qd.slot_base + p] = (uint16_t)key;
+            }
+            return;
+        }
+    } else {
+        t_zero(T0, lane);
+        __syncwarp();
+    }
+    unsigned long long in_acc = 0;
+    bool first = true;
+#pragma unroll 1
+    for (uint32_t i0 = 0; i0 < qd.k; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        uint64_t d = 0;
+        unsigned long long base = 0;
+        bool has = false;
+        if (i < qd.k) {
+            const BmView V = P.pool[mem[i]];
+            uint32_t j;
+            has = find_key(V, key, j);
+            if (has) {
+                d = __ldg(V.descs + j);
+                base = (unsigned long long)V.base;
+            }
+        }
+        uint32_t m = __ballot_sync(FULL, has);
+#pragma unroll 1
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const uint64_t ds = __shfl_sync(FULL, d, src);
+            const CRef x = cref(reinterpret_cast<const uint8_t *>(__shfl_sync(FULL, base, src)), ds);
+            in_acc += in_payload_bytes(ds) + 15;
+            if (is_and && first) t_decode(T0, x, lane);
+            else fold_into(T0, T1, x, qd.op, lane);
+            first = false;
+        }
+    }
+    unsigned long long card_acc = 0, words_acc = 0;
+    uint32_t bits_acc = 0;
+    emit_folded(es, qd, T0, T1, key, p, card_acc, words_acc, bits_acc, lane);
+    if (lane == 0) {
+        MStats *S = P.stats + q;
+        if (card_acc) atomicAdd(&S->card, card_acc);
+        if (words_acc) atomicAdd(&S->words, words_acc);
+        if (bits_acc) atomicAdd(&S->nbits, bits_acc);
+        if (in_acc) atomicAdd(&S->in_bytes, in_acc);
+    }
+    __syncwarp();
+}
+
 __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd, uint32_t local, uint64_t *T0,
                                 uint64_t *T1, MScratch *MS, uint32_t lane) {
     const uint32_t *mem = P.members + qd.mbase;
     const uint32_t k = qd.k;
     const uint32_t p0 = local * 32u;
-    uint32_t n_act, key = MKEY_END, pos = 0;
-    if (qd.op == OP_AND) {
-        n_act = p0 < qd.n_slots ? min(32u, qd.n_slots - p0) : 0u;
-        if (lane < n_act) {
-            key = __ldg(P.pool[mem[qd.driver]].keys + p0 + lane);
-            pos = p0 + lane;
-        }
-    } else {
-        const uint32_t npos = P.stats[q].n_pos;   // written by k_rank
-        n_act = p0 < npos ? min(32u, npos - p0) : 0u;
-        if (lane < n_act) {
-            pos = p0 + lane;
-            const uint32_t *pf = P.prefix + (size_t)qd.pres_idx * 1024;
-            uint32_t lo = 0, hi = 1024;   // the last word whose prefix is <= pos
-#pragma unroll 1
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (pf[mid] <= pos) lo = mid;
-                else hi = mid;
-            }
-            key = lo * 64 + nth_set_bit(P.pres[(size_t)qd.pres_idx * 1024 + lo], pos - pf[lo]);
-        }
-    }
+    uint32_t key = MKEY_END;
+    const uint32_t pos = p0 + lane;
+    const bool valid = out_key(P, q, qd, mem, pos, key);
+    const uint32_t n_act = __popc(__ballot_sync(FULL, valid));   // valid lanes are a prefix
     if (n_act == 0) return;
     MS->keys[lane] = key;
     __syncwarp();
@@ -611,8 +548,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_multi(MParams P) {
             else hi = mid;
         }
         const MultiDev qd = P.qs[lo];
-        if (qd.k <= MK) multi_tile_fast(P, lo, qd, (uint32_t)(t - P.tile_base[lo]), T0, T1, MS, lane);
-        else multi_tile(P, t, T0, T1, lane);
+        const uint32_t local = (uint32_t)(t - P.tile_base[lo]);
+        if (qd.k <= MK) multi_tile_fast(P, lo, qd, local, T0, T1, MS, lane);
+        else multi_key_wide(P, lo, qd, local, T0, T1, lane);
     }
 }
 
@@ -801,7 +739,9 @@ rb_status multi_prepare(const rb *const *pool, const BmView *d_pool, uint32_t po
             bcap += qb;
         }
         tb[q] = tiles;
-        tiles += (ns + 31) / 32;
+        // fast path: 32 output keys per tile; wide queries: one (the union has
+        // at most 65536 keys)
+        tiles += d.k <= MK ? (ns + 31) / 32 : (d.op == OP_OR ? std::min<uint64_t>(ns, 65536) : ns);
     }
     tb[nq] = tiles;
     b->n_items = (uint32_t)(items.size() / 2);
