@@ -129,6 +129,48 @@ rb_status rb_xor_cardinality(const rb_t *a, const rb_t *b, uint64_t *out, void *
 rb_status rb_jaccard(const rb_t *a, const rb_t *b, double *out, uint64_t *inter, uint64_t *uni,
                      void *stream);
 
+/* Cosine similarity |a n b| / sqrt(|a| |b|) (Sec. 5 "Fast counts" names it
+ * beside the Jaccard index).  |a n b| is counted on the device; *out is
+ * (double)|a n b| / sqrt((double)|a| * (double)|b|) with IEEE double
+ * operations, and 0.0 when either set is empty.  inter (may be NULL)
+ * receives |a n b|. */
+rb_status rb_cosine(const rb_t *a, const rb_t *b, double *out, uint64_t *inter, void *stream);
+
+/* -------------------------------------------------------- serialisation */
+
+/* A portable byte image of one bitmap, for snapshots of a resident index
+ * (Sec. 5 notes that Roaring has a portable serialized form but does not
+ * give it; this format is the library's own).  Little endian:
+ *   u32 magic 0x42474252, u32 version 1, u32 n (containers), u32 0,
+ *   u64 cardinality, u64 payload bytes,
+ *   u16 keys[n] (strictly increasing), u16 runs[n] (run containers: number
+ *   of runs, else 0), u8 types[n] (RB_TYPE_*), zero bytes to a multiple of
+ *   4, u32 cards[n], then every container's payload in key order exactly as
+ *   rb_export_layout writes it.
+ * rb_serialize: *n_bytes (may be NULL) gets the image size; with buf NULL
+ * nothing else happens, else the image is written to buf (host memory, cap
+ * bytes; RB_ERANGE if smaller).  Synchronises `stream`. */
+rb_status rb_serialize(const rb_t *b, uint8_t *buf, uint64_t cap, uint64_t *n_bytes, void *stream);
+/* A new bitmap from an image (host memory, len bytes).  Every field is
+ * checked on the host first (sizes, key order, sorted and maximal values
+ * and runs, cardinalities, the canonical type of each container); anything
+ * else returns RB_EINVAL and allocates nothing.  One upload on `stream`,
+ * synchronised before returning. */
+rb_status rb_deserialize(const uint8_t *buf, uint64_t len, void *stream, rb_t **out);
+
+/* ----------------------------------------------------------- membership */
+
+/* Membership of n values (Sec. 1: binary search over the 16-bit keys, then
+ * a bit test in a bitset or a search in an array or run container).
+ * out[i] = 1 if vals[i] is in b, else 0.  With on_device != 0, vals (n
+ * uint32) and out (n bytes) are device memory and the call only enqueues the
+ * work on `stream`; otherwise both are host memory, copied in and out, and
+ * the stream is synchronised.  n == 0 does nothing. */
+rb_status rb_contains_many(const rb_t *b, const uint32_t *vals, uint64_t n, int on_device, uint8_t *out,
+                           void *stream);
+/* One value: *out = 1 if value is in b, else 0 (synchronous, default stream). */
+rb_status rb_contains(const rb_t *b, uint32_t value, int *out);
+
 /* -------------------------------------------------------------- batches */
 
 /* One query of a batch: op (rb_op), indexes a and b into the pool, flags. */

@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (plain C99, portable flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _SRC, "-o", tmp])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -50,6 +50,9 @@ def _load():
         lib.orc_card.argtypes = [vp]
         lib.orc_jaccard.restype = ctypes.c_double
         lib.orc_jaccard.argtypes = [vp, vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        lib.orc_cosine.restype = ctypes.c_double
+        lib.orc_cosine.argtypes = [vp, vp, ctypes.POINTER(u64)]
+        lib.orc_contains.argtypes = [vp, vp, u64, vp]
         lib.orc_multi.restype = vp
         lib.orc_multi.argtypes = [i32, ctypes.POINTER(vp), u32]
         lib.orc_n.restype = u32
@@ -99,6 +102,18 @@ class Bitmap:
         i, u = ctypes.c_uint64(0), ctypes.c_uint64(0)
         j = _load().orc_jaccard(self._h, other._h, ctypes.byref(i), ctypes.byref(u))
         return j, int(i.value), int(u.value)
+
+    def cosine(self, other: "Bitmap"):
+        i = ctypes.c_uint64(0)
+        c = _load().orc_cosine(self._h, other._h, ctypes.byref(i))
+        return c, int(i.value)
+
+    def contains(self, values) -> np.ndarray:
+        v = np.ascontiguousarray(values, dtype=np.uint32)
+        out = np.zeros(v.size, dtype=np.uint8)
+        if v.size:
+            _load().orc_contains(self._h, v.ctypes.data, v.size, out.ctypes.data)
+        return out
 
     @staticmethod
     def multi(op: int, inputs) -> "Bitmap":

@@ -19,7 +19,9 @@
  *    values.  Empty containers are omitted (Sec. 2.2).
  *  - Sec. 1: intersection = AND, union = OR, difference = ANDNOT, symmetric
  *    difference = XOR.
- *  - Sec. 5 "Fast counts": Jaccard index |A n B| / |A u B|.
+ *  - Sec. 5 "Fast counts": Jaccard index |A n B| / |A u B| and cosine
+ *    similarity |A n B| / sqrt(|A| |B|).
+ *  - Sec. 1 / Sec. 5 "Membership queries": is x in the set?
  *  - Sec. 5 "Wide unions": the union of many sets, computed as a sequential
  *    fold over the inputs.
  *
@@ -41,6 +43,7 @@
  * (0 array, 1 bitset, 2 runs), card u32, and its payload bytes concatenated
  * in key order with offsets u64[n + 1].
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -256,6 +259,43 @@ double orc_jaccard(const obm *a, const obm *b, uint64_t *inter, uint64_t *uni) {
     *inter = orc_op_card(O_AND, a, b);
     *uni = orc_op_card(O_OR, a, b);
     return *uni ? (double)*inter / (double)*uni : 0.0;
+}
+
+/* Cosine similarity |A n B| / sqrt(|A| |B|) (Sec. 5 "Fast counts"), in IEEE
+ * double arithmetic; 0 when either set is empty. */
+double orc_cosine(const obm *a, const obm *b, uint64_t *inter) {
+    *inter = orc_op_card(O_AND, a, b);
+    uint64_t ca = orc_card(a), cb = orc_card(b);
+    if (ca == 0 || cb == 0) return 0.0;
+    return (double)*inter / sqrt((double)ca * (double)cb);
+}
+
+/* Membership of each value (Sec. 1): the chunk of the value's high 16 bits,
+ * then its low 16 bits within that chunk's container.  Plain scans: the
+ * containers in order, an array's values in order, each run in turn. */
+void orc_contains(const obm *b, const uint32_t *v, uint64_t n, uint8_t *out) {
+    for (uint64_t i = 0; i < n; i++) {
+        uint32_t key = v[i] >> 16, low = v[i] & 0xFFFF;
+        uint8_t r = 0;
+        for (uint32_t c = 0; c < b->n; c++) {
+            const ocont *x = &b->c[c];
+            if (x->key != key) continue;
+            if (x->type == O_BITSET) {
+                r = (x->data[low >> 3] >> (low & 7)) & 1;
+            } else if (x->type == O_ARRAY) {
+                for (uint32_t k = 0; k < x->card && !r; k++)
+                    r = (uint32_t)(x->data[2 * k] | (x->data[2 * k + 1] << 8)) == low;
+            } else {
+                for (uint32_t k = 0; k < x->nbytes / 4 && !r; k++) {
+                    uint32_t s = x->data[4 * k] | (x->data[4 * k + 1] << 8);
+                    uint32_t l = x->data[4 * k + 2] | (x->data[4 * k + 3] << 8);
+                    r = low >= s && low <= s + l;
+                }
+            }
+            break;
+        }
+        out[i] = r;
+    }
 }
 
 static obm *copy_bm(const obm *a) {

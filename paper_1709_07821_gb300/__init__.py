@@ -85,6 +85,11 @@ def _sig(L):
         "rb_and_cardinality": [vp, vp, pu64, vp], "rb_or_cardinality": [vp, vp, pu64, vp],
         "rb_andnot_cardinality": [vp, vp, pu64, vp], "rb_xor_cardinality": [vp, vp, pu64, vp],
         "rb_jaccard": [vp, vp, pdbl, pu64, pu64, vp],
+        "rb_cosine": [vp, vp, pdbl, pu64, vp],
+        "rb_contains_many": [vp, vp, u64, i32, vp, vp],
+        "rb_contains": [vp, u32, ctypes.POINTER(i32)],
+        "rb_serialize": [vp, vp, u64, pu64, vp],
+        "rb_deserialize": [vp, u64, vp, pvp],
         "rb_batch_op": [vp, u32, vp, u64, vp, vp, vp],
         "rb_batch_jaccard": [vp, u32, vp, vp, u64, vp, vp, vp, vp],
         "rb_plan_create": [vp, u32, vp, u64, vp, pvp],
@@ -263,6 +268,55 @@ class Bitmap:
         _check(lib().rb_jaccard(self._h, other._h, ctypes.byref(j), ctypes.byref(i), ctypes.byref(u),
                                 _stream(stream)))
         return j.value, i.value, u.value
+
+    def cosine(self, other: "Bitmap", stream=None):
+        """(|A n B| / sqrt(|A| |B|), |A n B|)."""
+        c, i = ctypes.c_double(), ctypes.c_uint64()
+        _check(lib().rb_cosine(self._h, other._h, ctypes.byref(c), ctypes.byref(i), _stream(stream)))
+        return c.value, i.value
+
+    def contains(self, values, stream=None):
+        """Membership of each value: a uint8 array (1 = present).  A CUDA
+        torch tensor of uint32/int32 values is answered on the device (the
+        result is a CUDA uint8 tensor on the same stream); anything else is
+        treated as host values."""
+        try:
+            import torch
+            is_dev = isinstance(values, torch.Tensor) and values.is_cuda
+        except Exception:
+            is_dev = False
+        if is_dev:
+            v = values.contiguous()
+            if v.dtype not in (torch.int32, torch.uint32):
+                raise TypeError("device values must be int32 or uint32")
+            out = torch.empty(v.numel(), dtype=torch.uint8, device=v.device)
+            _check(lib().rb_contains_many(self._h, v.data_ptr(), v.numel(), 1, out.data_ptr(), _stream(stream)))
+            return out
+        v = np.ascontiguousarray(values, dtype=np.uint32)
+        out = np.empty(v.size, dtype=np.uint8)
+        if v.size:
+            _check(lib().rb_contains_many(self._h, v.ctypes.data, v.size, 0, out.ctypes.data, _stream(stream)))
+        return out
+
+    def serialize(self, stream=None) -> bytes:
+        """The bitmap's portable byte image (format in include/rb.h)."""
+        n = ctypes.c_uint64()
+        _check(lib().rb_serialize(self._h, None, 0, ctypes.byref(n), _stream(stream)))
+        buf = (ctypes.c_uint8 * max(1, n.value))()
+        _check(lib().rb_serialize(self._h, buf, n.value, ctypes.byref(n), _stream(stream)))
+        return bytes(buf)[:n.value]
+
+    @classmethod
+    def deserialize(cls, data: bytes, stream=None) -> "Bitmap":
+        buf = (ctypes.c_uint8 * max(1, len(data))).from_buffer_copy(data if data else b"\0")
+        h = ctypes.c_void_p()
+        _check(lib().rb_deserialize(buf, len(data), _stream(stream), ctypes.byref(h)))
+        return cls(h.value)
+
+    def __contains__(self, value):
+        r = ctypes.c_int()
+        _check(lib().rb_contains(self._h, int(value), ctypes.byref(r)))
+        return bool(r.value)
 
     def __and__(self, o):
         return self.op(AND, o)

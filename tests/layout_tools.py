@@ -67,3 +67,20 @@ def check_canonical(lay):
                 assert r <= 2047
             else:
                 assert 2 * r < c
+
+
+def image_from_layout(lay):
+    """The portable byte image of a bitmap (the format include/rb.h
+    documents for rb_serialize), composed from an exported layout."""
+    import struct
+    keys, types, cards, offs, payload = lay["keys"], lay["types"], lay["cards"], lay["offs"], lay["payload"]
+    n = len(keys)
+    runs = np.zeros(n, np.uint16)
+    for i in range(n):
+        if types[i] == 2:
+            runs[i] = (int(offs[i + 1]) - int(offs[i])) // 4
+    head = struct.pack("<IIIIQQ", 0x42474252, 1, n, 0, int(cards.astype(np.uint64).sum()), len(payload))
+    body = keys.astype("<u2").tobytes() + runs.astype("<u2").tobytes() + types.astype(np.uint8).tobytes()
+    body += b"\0" * ((-len(body)) % 4)
+    body += cards.astype("<u4").tobytes()
+    return head + body + payload.tobytes()

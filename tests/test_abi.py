@@ -56,3 +56,55 @@ def test_argument_checks_without_gpu(librb):
     librb.rb_multi_op.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]
     assert librb.rb_multi_op(2, None, 0, None, None, None) == 1      # ANDNOT is not multi-way
+
+
+def test_deserialize_rejects_bad_images_without_gpu(librb, oracle_mod):
+    """rb_deserialize checks the whole image on the host before any device
+    work: images composed from the oracle's layout (the documented format),
+    each with one field broken, are refused with RB_EINVAL."""
+    import struct
+    import sys
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import numpy as np
+    from layout_tools import image_from_layout
+    vals = np.concatenate([np.arange(0, 62000, 62), np.arange(2**16, 2**16 + 100), np.arange(2**16 + 101, 2**16 + 201),
+                           np.arange(2 * 2**16, 3 * 2**16, 2)]).astype(np.uint32)
+    lay = oracle_mod.Bitmap.from_sorted(vals).layout()
+    img = image_from_layout(lay)
+    n = len(lay["keys"])
+    keys_at, runs_at, types_at = 32, 32 + 2 * n, 32 + 4 * n
+    cards_at = 32 + ((5 * n + 3) // 4) * 4
+    meta = cards_at + 4 * n
+    bad = {
+        "magic": b"XXXX" + img[4:],
+        "version": img[:4] + struct.pack("<I", 2) + img[8:],
+        "truncated": img[:-1],
+        "long": img + b"\0",
+        "keys_order": img[:keys_at] + struct.pack("<HH", 1, 0) + img[keys_at + 4:],
+        "type_out_of_range": img[:types_at] + bytes([3]) + img[types_at + 1:],
+        "card_mismatch": img[:cards_at] + struct.pack("<I", int(lay["cards"][0]) + 1) + img[cards_at + 4:],
+        "header_card": img[:16] + struct.pack("<Q", int(lay["cards"].sum()) + 1) + img[24:],
+        "array_unsorted": img[:meta] + img[meta + 2:meta + 4] + img[meta:meta + 2] + img[meta + 4:],
+        # the run chunk (2 runs) claimed as 1 run, or as 3
+        "run_count_low": img[:runs_at + 2] + struct.pack("<H", 1) + img[runs_at + 4:],
+        "run_count_high": img[:runs_at + 2] + struct.pack("<H", 3) + img[runs_at + 4:],
+        # the runs made adjacent: [2^16, 2^16 + 100) then [2^16 + 100, ...)
+        "runs_not_maximal": img[:meta + 2000 + 4] + struct.pack("<H", 100) + img[meta + 2000 + 6:],
+        # an array chunk retyped as runs: not canonical and the wrong size
+        "retyped": img[:types_at] + bytes([2]) + img[types_at + 1:],
+        "empty": b"",
+    }
+    librb.rb_deserialize.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+    for name, data in bad.items():
+        out = ctypes.c_void_p()
+        assert librb.rb_deserialize(data, len(data), None, ctypes.byref(out)) == 1, name
+        assert out.value is None, name
+    # a non-canonical but well-formed array: the first chunk's 1000 values
+    # replaced by 4097 consecutive ones as an array (canonically runs)
+    arr = np.arange(4097, dtype=np.uint16)
+    lay2 = {"keys": np.array([0], np.uint16), "types": np.array([0], np.uint8),
+            "cards": np.array([4097], np.uint32), "offs": np.array([0, 8194], np.uint64),
+            "payload": arr.view(np.uint8)}
+    data = image_from_layout(lay2)
+    out = ctypes.c_void_p()
+    assert librb.rb_deserialize(data, len(data), None, ctypes.byref(out)) == 1

@@ -248,3 +248,88 @@ def test_multi_way_mixed_types(rb, orc, workloads_mod):
             assert_layout_eq(m.layout(), exp.layout(), f"mixed op{op} k{k}")
             _, c2 = rb.multi_op(op, G[:k], count_only=True)
             assert c2 == exp.card
+
+
+def test_wide_union_and_intersection_of_200(rb, orc, workloads_mod):
+    """Sec. 5 "Wide unions": the union of all 200 bitmaps of the sparse
+    workload (cardinalities scaled to at most 10^4.5 so that the oracle's
+    sequential fold stays fast), and the intersection of bitmaps that share
+    a common subset, each in one multi-way evaluation."""
+    pool = _pool(workloads_mod, "sparse", 200, 4.5)
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    O = [orc.Bitmap.from_sorted(v) for v in vals]
+    m, card = rb.multi_op(1, G)
+    exp = orc.Bitmap.multi(1, O)
+    assert card == exp.card
+    assert_layout_eq(m.layout(), exp.layout(), "wide OR of 200")
+    common = np.arange(5, 2**24, 61, dtype=np.uint32)
+    V2 = [np.union1d(v, common).astype(np.uint32) for v in vals[:40]]
+    G2 = [rb.Bitmap.from_sorted(v) for v in V2]
+    O2 = [orc.Bitmap.from_sorted(v) for v in V2]
+    m2, c2 = rb.multi_op(0, G2)
+    exp2 = orc.Bitmap.multi(0, O2)
+    assert c2 == exp2.card
+    assert_layout_eq(m2.layout(), exp2.layout(), "wide AND of 40")
+
+
+def test_membership_and_cosine(rb, orc, workloads_mod):
+    """Batch membership (host and device values) and the cosine similarity
+    against the oracle, on a mixed pool: every container type, values inside
+    and just outside each chunk."""
+    import torch
+    pool = _pool(workloads_mod, "batched", 12, 5.5, seed=33)
+    vals = [pool.values(i) for i in range(pool.n)]
+    rng = np.random.default_rng(34)
+    for i in range(pool.n):
+        G, O = rb.Bitmap.from_sorted(vals[i]), orc.Bitmap.from_sorted(vals[i])
+        v = vals[i]
+        q = np.concatenate([v[::7], (v[::11] + 1).astype(np.uint32), (v[::13] - 1).astype(np.uint32),
+                            rng.integers(0, 2**32, 3000, dtype=np.uint64).astype(np.uint32),
+                            np.array([0, 65535, 65536, 0xFFFFFFFF], np.uint32)]).astype(np.uint32)
+        exp = O.contains(q)
+        assert np.array_equal(G.contains(q), exp), i
+        dq = torch.from_numpy(q.view(np.int32)).cuda()
+        got = G.contains(dq)
+        torch.cuda.synchronize()
+        assert np.array_equal(got.cpu().numpy(), exp), i
+        if len(v):
+            assert (int(v[len(v) // 2]) in G) and (int(v[0]) in G)
+    for i in range(pool.n - 1):
+        A, B = rb.Bitmap.from_sorted(vals[i]), rb.Bitmap.from_sorted(vals[i + 1])
+        OA, OB = orc.Bitmap.from_sorted(vals[i]), orc.Bitmap.from_sorted(vals[i + 1])
+        assert A.cosine(B) == OA.cosine(OB), i
+        assert A.cosine(A) == OA.cosine(OA), i
+    e = rb.Bitmap.from_sorted(np.zeros(0, np.uint32))
+    assert e.contains(np.array([0, 5], np.uint32)).tolist() == [0, 0]
+    assert e.cosine(e) == (0.0, 0)
+
+
+def test_serialize_roundtrip(rb, orc, workloads_mod):
+    """The byte image rb_serialize writes equals the one composed from the
+    oracle's layout by the documented format; rb_deserialize of it gives the
+    same canonical layout, and operations on it match the oracle."""
+    from layout_tools import image_from_layout
+    pool = _pool(workloads_mod, "batched", 10, 5.5, seed=41)
+    vals = [pool.values(i) for i in range(pool.n)] + [np.zeros(0, np.uint32), fig1_like()]
+    back = []
+    for i, v in enumerate(vals):
+        G, O = rb.Bitmap.from_sorted(v), orc.Bitmap.from_sorted(v)
+        img = G.serialize()
+        assert img == image_from_layout(O.layout()), i
+        D = rb.Bitmap.deserialize(img)
+        assert_layout_eq(D.layout(), O.layout(), f"roundtrip {i}")
+        assert D.card == O.card
+        back.append((D, O))
+    for i in range(len(back) - 1):
+        (D1, O1), (D2, O2) = back[i], back[i + 1]
+        for op in OPS:
+            assert_layout_eq(D1.op(op, D2).layout(), O1.op(op, O2).layout(), f"op {op} on {i}")
+
+
+def fig1_like():
+    arr = np.arange(1000, dtype=np.uint32) * 62
+    runs = np.concatenate([np.arange(2**16, 2**16 + 100), np.arange(2**16 + 101, 2**16 + 201),
+                           np.arange(2**16 + 300, 2**16 + 400)]).astype(np.uint32)
+    evens = np.arange(2 * 2**16, 3 * 2**16, 2, dtype=np.uint32)
+    return np.concatenate([arr, runs, evens])

@@ -245,3 +245,49 @@ def test_plain_workload_canonical(oracle_mod, workloads_mod):
         R = A.op(op, B)
         check_canonical(R.layout())
         assert np.array_equal(R.to_u32(), ref_op(op, a, b))
+
+
+def test_membership(oracle_mod):
+    """Sec. 1 membership on Fig. 1's bitmap (array, runs and bitset chunks),
+    at the values the figure describes and their neighbours, then against
+    numpy's isin on random sets."""
+    bm = oracle_mod.Bitmap.from_sorted(fig1_values())
+    probes = np.array([0, 62, 61938, 61939, 63, 2**16 - 1,            # multiples of 62 below 62,000
+                       2**16, 2**16 + 99, 2**16 + 100, 2**16 + 101,    # the gap at 2^16 + 100
+                       2**16 + 200, 2**16 + 201, 2**16 + 300, 2**16 + 399, 2**16 + 400,
+                       2 * 2**16, 2 * 2**16 + 1, 2 * 2**16 + 2, 3 * 2**16 - 2, 3 * 2**16 - 1,
+                       3 * 2**16, 0xFFFFFFFF], np.uint32)
+    want = [1, 1, 1, 0, 0, 0,
+            1, 1, 0, 1,
+            1, 0, 1, 1, 0,
+            1, 0, 1, 1, 0,
+            0, 0]
+    assert bm.contains(probes).tolist() == want
+    rng = np.random.default_rng(5)
+    for _ in range(10):
+        a = random_set(rng, 4)
+        q = np.concatenate([a[::3], rng.integers(0, 5 * 2**16, 500, dtype=np.uint32),
+                            (a[::5] + 1).astype(np.uint32)]).astype(np.uint32)
+        A = oracle_mod.Bitmap.from_sorted(a)
+        assert np.array_equal(A.contains(q), np.isin(q, a).astype(np.uint8))
+
+
+def test_cosine(oracle_mod):
+    """Sec. 5 "Fast counts": cosine similarity |A n B| / sqrt(|A| |B|),
+    against the closed form over numpy's intersection (one correctly rounded
+    product, square root and quotient), and its special cases."""
+    import math
+    rng = np.random.default_rng(17)
+    for _ in range(20):
+        a, b = random_set(rng, 4), random_set(rng, 4)
+        A, B = oracle_mod.Bitmap.from_sorted(a), oracle_mod.Bitmap.from_sorted(b)
+        c, i = A.cosine(B)
+        ii = len(np.intersect1d(a, b))
+        assert i == ii
+        assert c == (ii / math.sqrt(len(a) * len(b)) if len(a) and len(b) else 0.0)
+    f = oracle_mod.Bitmap.from_sorted(fig1_values())
+    assert f.cosine(f) == (1.0, len(fig1_values()))
+    e = oracle_mod.Bitmap.from_sorted([])
+    assert f.cosine(e) == (0.0, 0) and e.cosine(e) == (0.0, 0)
+    odd = oracle_mod.Bitmap.from_sorted(np.arange(1, 3 * 2**16, 2, dtype=np.uint32))
+    assert f.cosine(odd)[1] == len(np.intersect1d(fig1_values(), np.arange(1, 3 * 2**16, 2)))

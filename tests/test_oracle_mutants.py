@@ -26,6 +26,9 @@ MUTANTS = {
                   "out->data[v[i] >> 3] |= (uint8_t)(0x80u >> (v[i] & 7));"),
     "jaccard_via_xor": ("*uni = orc_op_card(O_OR, a, b);", "*uni = orc_op_card(O_XOR, a, b);"),
     "fold_skips_last": ("for (uint32_t i = 1; i < k && acc; i++) {", "for (uint32_t i = 1; i + 1 < k && acc; i++) {"),
+    "run_end_exclusive": ("r = low >= s && low <= s + l;", "r = low >= s && low < s + l;"),
+    "cosine_sum": ("return (double)*inter / sqrt((double)ca * (double)cb);",
+                   "return (double)*inter / sqrt((double)ca + (double)cb);"),
 }
 
 RUNNER = r"""
@@ -37,7 +40,8 @@ import test_oracle as T
 fails = 0
 for name in ["test_fig1_layout", "test_difference_example", "test_dedup_example",
              "test_array_bitset_union_example", "test_type_thresholds",
-             "test_count_identities_and_jaccard", "test_multi_way_fold", "test_edges"]:
+             "test_count_identities_and_jaccard", "test_multi_way_fold", "test_edges",
+             "test_membership", "test_cosine"]:
     try:
         getattr(T, name)(oracle)
     except Exception:
