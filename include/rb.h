@@ -291,6 +291,20 @@ rb_status rb_server_submit(rb_server_t *s, const rb_request *r, uint64_t *ticket
  * RB_ETIMEOUT if it is not done in time (the ticket stays valid). */
 rb_status rb_server_wait(rb_server_t *s, uint64_t ticket, int timeout_ms, rb_t **out,
                          uint64_t *card, double *latency_s);
+/* Queue n requests at once (a frontend draining its input in bursts): the
+ * same checks as rb_server_submit for every request, then all are queued
+ * with one lock and the same submit time; tickets[i] is request i's ticket.
+ * On a bad request nothing is queued and its error is returned. */
+rb_status rb_server_submit_many(rb_server_t *s, const rb_request *r, uint32_t n, uint64_t *tickets);
+/* Collect up to cap completed requests in completion order, waiting at most
+ * timeout_ms for the first one; *n_out gets how many (0 on timeout).  For
+ * each: tickets[i], status[i] (RB_OK or the request's error), outs[i] (the
+ * result bitmap of a materialising request, owned by the caller; NULL
+ * otherwise; with outs == NULL every result is freed at once), cards[i],
+ * latency_s[i] (submit to completion on the device).  status, outs, cards
+ * and latency_s may be NULL.  A collected ticket is no longer valid. */
+rb_status rb_server_poll(rb_server_t *s, uint32_t cap, int timeout_ms, uint64_t *tickets, rb_status *status,
+                         rb_t **outs, uint64_t *cards, double *latency_s, uint32_t *n_out);
 /* Counters: completed requests, launched batches, peak requests in flight. */
 rb_status rb_server_stats(rb_server_t *s, uint64_t *completed, uint64_t *batches,
                           uint64_t *peak_inflight);

@@ -102,6 +102,8 @@ def _sig(L):
         "rb_server_create": [vp, u32, u64, u32, u32, pvp],
         "rb_server_submit": [vp, ctypes.POINTER(Request), pu64],
         "rb_server_wait": [vp, u64, i32, pvp, pu64, pdbl],
+        "rb_server_submit_many": [vp, ctypes.POINTER(Request), u32, pu64],
+        "rb_server_poll": [vp, u32, i32, pu64, vp, pvp, pu64, pdbl, pu32],
         "rb_server_stats": [vp, pu64, pu64, pu64],
         "rb_selftest_wait": [u64, ctypes.c_int, vp],
     }
@@ -521,6 +523,43 @@ class Server:
         t = ctypes.c_uint64()
         _check(lib().rb_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value
+
+    def submit_many(self, ops, ks, count_only, members) -> np.ndarray:
+        """Queue n requests in one call: ops[i], ks[i] members from row i of
+        members (an n x SERVE_MAX_K array), count_only[i]; returns the
+        tickets (uint64)."""
+        n = len(ops)
+        reqs = (Request * max(1, n))()
+        mem = np.asarray(members)
+        for i in range(n):
+            r = reqs[i]
+            r.op = int(ops[i])
+            r.k = int(ks[i])
+            r.count_only = 1 if count_only[i] else 0
+            for j in range(min(int(ks[i]), SERVE_MAX_K)):
+                r.members[j] = int(mem[i, j])
+        t = np.zeros(max(1, n), np.uint64)
+        if n:
+            _check(lib().rb_server_submit_many(self._h, reqs, n,
+                                               t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return t[:n]
+
+    def poll(self, cap: int = 1024, timeout_ms: int = 100, want_bitmaps: bool = False):
+        """Up to cap completed requests: (tickets, statuses, cards, latencies
+        in seconds, bitmaps or None).  Without want_bitmaps the results are
+        freed inside the library."""
+        t = np.zeros(cap, np.uint64)
+        st = np.zeros(cap, np.int32)
+        c = np.zeros(cap, np.uint64)
+        lat = np.zeros(cap, np.float64)
+        outs = (ctypes.c_void_p * cap)() if want_bitmaps else None
+        n = ctypes.c_uint32()
+        u64p, dp = ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)
+        _check(lib().rb_server_poll(self._h, cap, timeout_ms, t.ctypes.data_as(u64p), st.ctypes.data,
+                                    outs, c.ctypes.data_as(u64p), lat.ctypes.data_as(dp), ctypes.byref(n)))
+        k = n.value
+        bms = [Bitmap(outs[i]) if outs[i] else None for i in range(k)] if want_bitmaps else None
+        return t[:k], st[:k], c[:k], lat[:k], bms
 
     def wait(self, ticket: int, timeout_ms: int = 60000, want_bitmap: bool = True):
         h = ctypes.c_void_p()

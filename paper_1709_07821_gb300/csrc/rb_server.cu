@@ -58,6 +58,7 @@ struct rb_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
+    std::deque<uint64_t> done;   // completed tickets in completion order (rb_server_poll)
     std::unordered_map<uint64_t, Req> reqs;
     std::vector<Slot> slots;
     std::list<Flight *> flights;
@@ -103,6 +104,15 @@ void retire(rb_server *S, Flight *f) {
         r.card = cards[i];
         r.latency = std::chrono::duration<double>(f->t_done - r.t_submit).count();
         r.state = 2;
+        S->done.push_back(f->tickets[i]);
+    }
+    // tickets collected by rb_server_wait stay in `done` until a poll skips
+    // them; drop them here when they pile up
+    if (S->done.size() > 4096 && S->done.size() > 2 * S->reqs.size()) {
+        std::deque<uint64_t> keep;
+        for (uint64_t t : S->done)
+            if (S->reqs.count(t)) keep.push_back(t);
+        S->done.swap(keep);
     }
     S->completed += f->tickets.size();
     S->inflight -= f->tickets.size();
@@ -131,7 +141,11 @@ void loop(rb_server *S) {
             // shutting down: requests never admitted fail with RB_EBUSY
             for (uint64_t t : S->queue) {
                 auto it = S->reqs.find(t);
-                if (it != S->reqs.end()) { it->second.st = RB_EBUSY; it->second.state = 2; }
+                if (it != S->reqs.end()) {
+                    it->second.st = RB_EBUSY;
+                    it->second.state = 2;
+                    S->done.push_back(t);
+                }
             }
             S->queue.clear();
             S->cv_done.notify_all();
@@ -198,7 +212,11 @@ void loop(rb_server *S) {
                 cudaStreamSynchronize(sl.s);
                 for (uint64_t t : tk) {
                     auto it = S->reqs.find(t);
-                    if (it != S->reqs.end()) { it->second.st = st; it->second.state = 2; }
+                    if (it != S->reqs.end()) {
+                        it->second.st = st;
+                        it->second.state = 2;
+                        S->done.push_back(t);
+                    }
                 }
                 if (f->mb) multi_free(f->mb, sl.s);
                 arena_unref(f->arena);
@@ -261,8 +279,12 @@ rb_status rb_server_create(const rb_t *const *index, uint32_t n, uint64_t mem_bu
     return RB_OK;
 }
 
-rb_status rb_server_submit(rb_server_t *S, const rb_request *r, uint64_t *ticket) {
-    if (!S || !r || !ticket) return set_err(RB_EINVAL, "rb_server_submit: NULL argument");
+}  // extern "C"
+
+namespace {
+
+// checks one request and computes its worst-case result bytes
+rb_status make_req(rb_server_t *S, const rb_request *r, Req &q) {
     if (r->op != RB_AND && r->op != RB_OR) return set_err(RB_EINVAL, "request op must be RB_AND or RB_OR");
     if (r->k < 1 || r->k > RB_SERVE_MAX_K) return set_err(RB_EINVAL, "request k must be 1..%d", RB_SERVE_MAX_K);
     MultiQuery mq;
@@ -272,19 +294,70 @@ rb_status rb_server_submit(rb_server_t *S, const rb_request *r, uint64_t *ticket
         if (r->members[i] >= S->n) return set_err(RB_EINVAL, "request member %u out of range", r->members[i]);
         mq.members.push_back(r->members[i]);
     }
-    Req q;
     q.r = *r;
     q.bound = multi_query_bound(S->index.data(), mq);
     if (q.bound > S->budget_cap) return set_err(RB_EBUSY, "request needs up to %llu bytes, above the whole budget",
                                                 (unsigned long long)q.bound);
-    q.t_submit = clk::now();
+    return RB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rb_status rb_server_submit(rb_server_t *S, const rb_request *r, uint64_t *ticket) {
+    if (!S || !r || !ticket) return set_err(RB_EINVAL, "rb_server_submit: NULL argument");
+    return rb_server_submit_many(S, r, 1, ticket);
+}
+
+rb_status rb_server_submit_many(rb_server_t *S, const rb_request *r, uint32_t n, uint64_t *tickets) {
+    if (!S || (n && (!r || !tickets))) return set_err(RB_EINVAL, "rb_server_submit_many: NULL argument");
+    std::vector<Req> qs(n);
+    for (uint32_t i = 0; i < n; i++) {
+        rb_status st = make_req(S, r + i, qs[i]);
+        if (st != RB_OK) return st;
+    }
+    const clk::time_point now = clk::now();
     {
         std::lock_guard<std::mutex> g(S->mu);
-        *ticket = S->next_ticket++;
-        S->reqs.emplace(*ticket, q);
-        S->queue.push_back(*ticket);
+        for (uint32_t i = 0; i < n; i++) {
+            qs[i].t_submit = now;
+            tickets[i] = S->next_ticket++;
+            S->reqs.emplace(tickets[i], qs[i]);
+            S->queue.push_back(tickets[i]);
+        }
     }
     S->cv_work.notify_all();
+    return RB_OK;
+}
+
+rb_status rb_server_poll(rb_server_t *S, uint32_t cap, int timeout_ms, uint64_t *tickets, rb_status *status,
+                         rb_t **outs, uint64_t *cards, double *latency_s, uint32_t *n_out) {
+    if (!S || !n_out || (cap && !tickets)) return set_err(RB_EINVAL, "rb_server_poll: NULL argument");
+    *n_out = 0;
+    std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = clk::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (S->done.empty()) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && S->done.empty()) return RB_OK;
+    }
+    uint32_t k = 0;
+    while (k < cap && !S->done.empty()) {
+        const uint64_t t = S->done.front();
+        S->done.pop_front();
+        auto it = S->reqs.find(t);
+        if (it == S->reqs.end()) continue;   // already collected by rb_server_wait
+        Req &q = it->second;
+        tickets[k] = t;
+        if (status) status[k] = q.st;
+        if (cards) cards[k] = q.st == RB_OK ? q.card : 0;
+        if (latency_s) latency_s[k] = q.latency;
+        if (outs) outs[k] = q.st == RB_OK ? q.out : nullptr;
+        else rb_free(q.out);
+        if (outs && q.st != RB_OK) rb_free(q.out);
+        S->reqs.erase(it);
+        k++;
+    }
+    *n_out = k;
     return RB_OK;
 }
 

@@ -121,3 +121,41 @@ def test_bad_requests(env):
             srv.submit(rb.AND, list(range(9)))         # more than 8 members
     finally:
         srv.close()
+
+
+def test_bulk_submit_and_poll(env):
+    """Requests handed over in bursts (rb_server_submit_many) and collected
+    in bursts (rb_server_poll) give the same results as each request alone
+    and as the oracle; every ticket comes back exactly once."""
+    rb, orc, W, pool, G, O = env
+    ops, ks, co, mem = W.multi_queries(53, 150, pool.n)
+    srv = rb.Server(G, mem_budget=8 << 30, max_inflight_batches=4, max_batch=32)
+    try:
+        tickets = np.concatenate([srv.submit_many(ops[i:i + 37], ks[i:i + 37], co[i:i + 37], mem[i:i + 37])
+                                  for i in range(0, len(ops), 37)])
+        assert len(np.unique(tickets)) == len(ops)
+        seen = {}
+        while len(seen) < len(ops):
+            t, st, cards, lat, bms = srv.poll(cap=16, timeout_ms=60000, want_bitmaps=True)
+            assert len(t) > 0
+            for x, s, c, l, bm in zip(t, st, cards, lat, bms):
+                assert s == 0 and l > 0 and int(x) not in seen
+                seen[int(x)] = (int(c), bm)
+        for q in range(len(ops)):
+            card, bm = seen[int(tickets[q])]
+            members = mem[q, :ks[q]].tolist()
+            exp = orc.Bitmap.multi(int(ops[q]), [O[m] for m in members])
+            assert card == exp.card, q
+            if co[q]:
+                assert bm is None
+            else:
+                lay, ref = bm.layout(), exp.layout()
+                for k in ("keys", "types", "cards", "offs", "payload"):
+                    assert np.array_equal(lay[k], ref[k]), (q, k)
+                bm.free()
+        t, _, _, _, _ = srv.poll(cap=4, timeout_ms=10)
+        assert len(t) == 0
+        with pytest.raises(rb.RoaringError):
+            srv.submit_many([rb.XOR], [2], [0], np.zeros((1, 8), np.uint32))
+    finally:
+        srv.close()
