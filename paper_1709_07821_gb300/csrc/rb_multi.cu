@@ -50,7 +50,8 @@ struct MParams {
     MStats *stats;
     MState *es;
     unsigned long long n_tiles;
-    uint32_t n_q, pad;
+    uint32_t n_q;
+    uint32_t chunk;   // consecutive tiles a warp takes at once
 };
 
 __device__ __forceinline__ bool find_key(const BmView &V, uint32_t key, uint32_t &j) {
@@ -125,7 +126,11 @@ struct MScratch {
     uint32_t ix[MK][32];       // container of output key `lane` in member i (NOIX: none)
     uint32_t keys[32];         // the tile's output keys (MKEY_END past the last)
     uint32_t lo[MK], hi[MK];   // each member's keys within the tile's key range
+    // what the warp's previous tile leaves to the next one of the same query:
+    // its query, the next tile index, and (OR) the presence word of its last key
+    uint32_t c_q, c_next, c_word, pad;
 };
+constexpr uint32_t MCHUNK = 4;   // most consecutive tiles a warp takes at once (large batches)
 constexpr uint32_t WARP_SMEM = 16384 + sizeof(MScratch);
 
 // index of the n-th (from 0) set bit of x, n < popcount(x)
@@ -159,6 +164,17 @@ __device__ __forceinline__ uint32_t lower_bound_u16(const uint16_t *a, uint32_t 
         else hi = m;
     }
     return lo;
+}
+
+// first index i >= start of sorted keys[0..n) with keys[i] >= key, looking at
+// the 32 keys from start first (one or two cache lines) and searching the
+// rest only if they are all smaller
+__device__ __forceinline__ uint32_t lb_from(const uint16_t *keys, uint32_t n, uint32_t start, uint32_t key) {
+    if (start >= n) return n;
+    const uint32_t w = min(n - start, 32u);
+    const uint32_t r = lower_bound16(keys + start, w, key);
+    if (r < w || start + w == n) return start + r;
+    return start + w + lower_bound16(keys + start + w, n - start - w, key);
 }
 
 // count c, runs r and canonical encoding of a lane's column X[0..n); writes
@@ -342,19 +358,62 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
     const uint32_t *mem = P.members + qd.mbase;
     const uint32_t k = qd.k;
     const uint32_t p0 = local * 32u;
+    const bool cont = MS->c_q == q && MS->c_next == local;   // the previous tile of this warp precedes this one
     uint32_t key = MKEY_END;
     const uint32_t pos = p0 + lane;
-    const bool valid = out_key(P, q, qd, mem, pos, key);
+    bool valid;
+    if (qd.op == OP_AND) {
+        valid = out_key(P, q, qd, mem, pos, key);
+    } else {
+        // OR: the word of the presence bitmap holding the pos-th key, searched
+        // in a window of 32 words that starts at the previous tile's last
+        // word (or at the word of p0, found by a 32-ary search)
+        const uint32_t npos = P.stats[q].n_pos;
+        valid = pos < npos;
+        if (p0 >= npos) return;
+        const uint32_t *pf = P.prefix + (size_t)qd.pres_idx * 1024;
+        uint32_t w0 = cont ? MS->c_word : 0;
+        if (!cont) {
+            uint32_t m = __ballot_sync(FULL, pf[32 * lane] <= p0);
+            const uint32_t b = 31 - __clz(m);
+            m = __ballot_sync(FULL, pf[32 * b + lane] <= p0);
+            w0 = 32 * b + 31 - __clz(m);
+        }
+        const uint32_t pw = w0 + lane < 1024 ? pf[w0 + lane] : 0xFFFFFFFFu;
+        uint32_t j = 0;   // the last window word whose prefix is <= pos
+#pragma unroll
+        for (uint32_t st = 16; st; st >>= 1)
+            if (__shfl_sync(FULL, pw, j + st) <= pos) j += st;
+        uint32_t w = w0 + j;
+        if (valid && j == 31 && w0 + 32 < 1024 && pf[w0 + 32] <= pos) {   // past the window
+            uint32_t lo = w0 + 32, hi = 1024;
+#pragma unroll 1
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (pf[mid] <= pos) lo = mid;
+                else hi = mid;
+            }
+            w = lo;
+        }
+        if (valid) key = w * 64 + nth_set_bit(P.pres[(size_t)qd.pres_idx * 1024 + w], pos - pf[w]);
+    }
     const uint32_t n_act = __popc(__ballot_sync(FULL, valid));   // valid lanes are a prefix
     if (n_act == 0) return;
     MS->keys[lane] = key;
     __syncwarp();
     const uint32_t k_lo = MS->keys[0], k_hi = MS->keys[n_act - 1];
     if (lane < k) {
+        // each member's keys in [k_lo, k_hi]: continuing tiles start where the
+        // previous tile's range ended
         const BmView V = P.pool[mem[lane]];
-        const uint32_t lo = lower_bound16(V.keys, V.n, k_lo);
+        const uint32_t lo = cont ? lb_from(V.keys, V.n, MS->hi[lane], k_lo) : lower_bound16(V.keys, V.n, k_lo);
         MS->lo[lane] = lo;
-        MS->hi[lane] = lo + lower_bound16(V.keys + lo, V.n - lo, k_hi + 1);
+        MS->hi[lane] = lb_from(V.keys, V.n, lo, k_hi + 1);
+    }
+    if (lane == n_act - 1) {
+        MS->c_q = q;
+        MS->c_next = local + 1;
+        MS->c_word = key >> 6;
     }
     for (uint32_t i = 0; i < k; i++) MS->ix[i][lane] = NOIX;
     __syncwarp();
@@ -536,21 +595,34 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_multi(MParams P) {
     uint64_t *T0 = smem + (size_t)warp * (WARP_SMEM / 8);
     uint64_t *T1 = T0 + 1024;
     MScratch *MS = reinterpret_cast<MScratch *>(T0 + 2048);
+    if (lane == 0) MS->c_q = 0xFFFFFFFFu;
+    __syncwarp();
+    unsigned long long t = 0, t_end = 0, q_lo = 0, q_hi = 0;
+    uint32_t q = 0;
     for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(&P.es->work, 1ull);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= P.n_tiles) break;
-        uint32_t lo = 0, hi = P.n_q;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (P.tile_base[mid] <= t) lo = mid;
-            else hi = mid;
+        if (t == t_end) {
+            if (lane == 0) t = atomicAdd(&P.es->work, (unsigned long long)P.chunk);
+            t = __shfl_sync(FULL, t, 0);
+            if (t >= P.n_tiles) break;
+            t_end = min(t + P.chunk, P.n_tiles);
         }
-        const MultiDev qd = P.qs[lo];
-        const uint32_t local = (uint32_t)(t - P.tile_base[lo]);
-        if (qd.k <= MK) multi_tile_fast(P, lo, qd, local, T0, T1, MS, lane);
-        else multi_key_wide(P, lo, qd, local, T0, T1, lane);
+        if (t < q_lo || t >= q_hi) {
+            uint32_t lo = 0, hi = P.n_q;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (P.tile_base[mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            q = lo;
+            q_lo = P.tile_base[lo];
+            q_hi = P.tile_base[lo + 1];
+        }
+        const MultiDev qd = P.qs[q];
+        const uint32_t local = (uint32_t)(t - q_lo);
+        if (qd.k <= MK) multi_tile_fast(P, q, qd, local, T0, T1, MS, lane);
+        else multi_key_wide(P, q, qd, local, T0, T1, lane);
+        __syncwarp();
+        t++;
     }
 }
 
@@ -841,7 +913,12 @@ static void launch_multi_w(const MParams &P, int ctas, cudaStream_t s) {
     }
     unsigned long long need = (P.n_tiles + W - 1) / W, cap = (unsigned long long)sm_count() * ctas;
     unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min(need, cap));
-    k_multi<W><<<grid, W * 32, smem, s>>>(P);
+    // chunks of consecutive tiles only when every warp has many tiles: a
+    // small batch keeps one tile per warp at a time, for latency
+    MParams Q = P;
+    const unsigned long long per_warp = P.n_tiles / ((unsigned long long)grid * W);
+    Q.chunk = per_warp >= 8ull * MCHUNK ? MCHUNK : 1;
+    k_multi<W><<<grid, W * 32, smem, s>>>(Q);
 }
 
 rb_status multi_enqueue(MultiBatch *b, RbArena *arena, cudaStream_t s) {
@@ -881,7 +958,7 @@ rb_status multi_enqueue(MultiBatch *b, RbArena *arena, cudaStream_t s) {
     P.es = b->d_es;
     P.n_tiles = b->total_tiles;
     P.n_q = nq;
-    P.pad = 0;
+    P.chunk = 1;
     const rb_schedule sc = current_schedule();
     if (b->total_tiles) {
         switch (sc.warps_per_cta) {
