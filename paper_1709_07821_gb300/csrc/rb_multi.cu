@@ -126,6 +126,7 @@ struct MScratch {
     uint32_t ix[MK][32];       // container of output key `lane` in member i (NOIX: none)
     uint32_t keys[32];         // the tile's output keys (MKEY_END past the last)
     uint32_t lo[MK], hi[MK];   // each member's keys within the tile's key range
+    const uint64_t *bp[MK];    // the bitsets of the key being folded
     // what the warp's previous tile leaves to the next one of the same query:
     // its query, the next tile index, and (OR) the presence word of its last key
     uint32_t c_q, c_next, c_word, pad;
@@ -211,12 +212,46 @@ __device__ __forceinline__ void col_emit(uint64_t *X, uint32_t n, uint32_t ty, u
     }
 }
 
+// T0 = T0 op B_0 op ... op B_{nb-1} over the bitsets at bp[0..nb) (from 0
+// instead of T0 when from_zero), counting the result's cardinality c and
+// maximal runs r in the same pass; every bitset's words of a stripe are
+// requested together, so the members' loads overlap
+__device__ __noinline__ void fuse_bitsets(uint64_t *T0, const uint64_t *const *bp, uint32_t nb, uint32_t op,
+                                          bool from_zero, uint32_t &c, uint32_t &r, uint32_t lane) {
+    ulonglong2 *D = reinterpret_cast<ulonglong2 *>(T0);
+    uint32_t cc = 0, rr = 0, carry = 0;
+#pragma unroll 2
+    for (int k = 0; k < 16; k++) {
+        ulonglong2 y[MK];
+#pragma unroll
+        for (uint32_t m = 0; m < MK; m++)
+            if (m < nb) y[m] = __ldg(reinterpret_cast<const ulonglong2 *>(bp[m]) + 32 * k + lane);
+        ulonglong2 x = from_zero ? make_ulonglong2(op == OP_AND ? ~0ull : 0ull, op == OP_AND ? ~0ull : 0ull)
+                                 : D[32 * k + lane];
+#pragma unroll
+        for (uint32_t m = 0; m < MK; m++)
+            if (m < nb) {
+                x.x = apply_op(op, x.x, y[m].x);
+                x.y = apply_op(op, x.y, y[m].y);
+            }
+        D[32 * k + lane] = x;
+        cc += __popcll(x.x) + __popcll(x.y);
+        const uint32_t top = (uint32_t)(x.y >> 63);
+        uint32_t prev = __shfl_up_sync(FULL, top, 1);
+        if (lane == 0) prev = carry;
+        carry = __shfl_sync(FULL, top, 31);
+        rr += __popcll(x.x & ~((x.x << 1) | (uint64_t)prev)) + __popcll(x.y & ~((x.y << 1) | (x.x >> 63)));
+    }
+    c = warp_sum(cc);
+    r = warp_sum(rr);
+    __syncwarp();
+}
+
 // after the warp folded one key into T0: count, canonical type, emit, record
 __device__ void emit_folded(MState *es, const MultiDev &qd, uint64_t *T0, uint64_t *T1, uint32_t key, uint32_t pos,
                             unsigned long long &card_acc, unsigned long long &words_acc, uint32_t &bits_acc,
-                            uint32_t lane) {
-    uint32_t c, r;
-    t_combine<false>(nullptr, T0, T0, OP_OR, c, r, lane);
+                            uint32_t lane, bool counted = false, uint32_t c = 0, uint32_t r = 0) {
+    if (!counted) t_combine<false>(nullptr, T0, T0, OP_OR, c, r, lane);
     __syncwarp();
     if (qd.count_only) {
         if (lane == 0) card_acc += c;
@@ -553,25 +588,40 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
         wl &= wl - 1;
         const uint32_t k_key = __shfl_sync(FULL, key, src), k_pos = __shfl_sync(FULL, pos, src);
         const uint32_t k_min = __shfl_sync(FULL, min_i, src);
-        if (is_and) {
-            const BmView D = P.pool[mem[k_min]];
-            t_decode(T0, cref(D.base, __ldg(D.descs + MS->ix[k_min][src])), lane);
-            for (uint32_t i = 0; i < k; i++) {
-                if (i == k_min) continue;
-                const BmView V = P.pool[mem[i]];
-                fold_into(T0, T1, cref(V.base, __ldg(V.descs + MS->ix[i][src])), OP_AND, lane);
-            }
-        } else {
-            t_zero(T0, lane);
-            __syncwarp();
-            for (uint32_t i = 0; i < k; i++) {
-                const uint32_t j = MS->ix[i][src];
-                if (j == NOIX) continue;
-                const BmView V = P.pool[mem[i]];
-                fold_into(T0, T1, cref(V.base, __ldg(V.descs + j)), OP_OR, lane);
+        // arrays and runs are folded into T0 one by one; the bitsets are
+        // combined in one pass at the end, which also counts the result
+        // (AND starts from the smallest container unless it is a bitset)
+        uint32_t nb = 0;
+        bool started = false;
+        for (uint32_t i = 0; i < k; i++) {
+            const uint32_t j = MS->ix[i][src];
+            if (j == NOIX) continue;
+            const BmView V = P.pool[mem[i]];
+            const CRef x = cref(V.base, __ldg(V.descs + j));
+            if (x.type == T_BITSET) {
+                if (lane == 0) MS->bp[nb] = reinterpret_cast<const uint64_t *>(x.p);
+                nb++;
+            } else if (!started) {
+                if (is_and) {
+                    t_decode(T0, x, lane);
+                } else {
+                    t_zero(T0, lane);
+                    __syncwarp();
+                    fold_into(T0, T1, x, OP_OR, lane);
+                }
+                started = true;
+            } else {
+                fold_into(T0, T1, x, is_and ? OP_AND : OP_OR, lane);
             }
         }
-        emit_folded(es, qd, T0, T1, k_key, k_pos, card_acc, words_acc, bits_acc, lane);
+        __syncwarp();
+        uint32_t c = 0, r = 0;
+        if (nb) {
+            fuse_bitsets(T0, MS->bp, nb, is_and ? OP_AND : OP_OR, !started, c, r, lane);
+            emit_folded(es, qd, T0, T1, k_key, k_pos, card_acc, words_acc, bits_acc, lane, true, c, r);
+        } else {
+            emit_folded(es, qd, T0, T1, k_key, k_pos, card_acc, words_acc, bits_acc, lane);
+        }
     }
     // per-query sums
     card_acc = warp_sum64(card_acc);
