@@ -41,6 +41,9 @@ namespace {
 constexpr uint32_t F_COUNT = 1, F_MERGE = 2;
 enum : uint32_t { K_NONE = 0, K_EMPTY = 1, K_PAIR = 2, K_COPY_A = 3, K_COPY_B = 4 };
 constexpr int LEAN_THREADS = 128;
+// resident k_lean CTAs per SM: the register bound (72 per thread) that keeps
+// the kernel free of most spills
+constexpr uint32_t LEAN_CTAS_MAX = 7;
 constexpr uint32_t KEY_END = 0x10000u;   // past-the-end key sentinel
 // algorithmic bytes of a container's key and metadata (key 2, type 1,
 // cardinality 4, payload offset 8), whatever the layout packs them into,
@@ -963,7 +966,7 @@ __device__ __noinline__ uint32_t group_count_arrays(const uint16_t *ga, uint32_t
 // Group-sized array merges of the lanes in gq, GPER at a time: group g of
 // lanes takes the g-th of the next GPER queued pairs; each served lane gets
 // its pair's descriptor and cardinality
-__device__ __noinline__ void process_groups(ExecState *es, uint32_t gq, const CRef &ca, const CRef &cb, uint32_t tbl,
+__device__ __forceinline__ void process_groups(ExecState *es, uint32_t gq, const CRef &ca, const CRef &cb, uint32_t tbl,
                                             uint64_t off, bool count, uint16_t *stg, uint32_t lane, uint64_t &desc,
                                             uint32_t &card) {
     const uint32_t g = lane / GW, sl = lane % GW;
@@ -1152,7 +1155,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     }
 }
 
-__global__ void __launch_bounds__(LEAN_THREADS, 8) k_lean(PairParams P) {
+__global__ void __launch_bounds__(LEAN_THREADS, LEAN_CTAS_MAX) k_lean(PairParams P) {
     __shared__ uint32_t s_win[LEAN_THREADS / 32][66];
     __shared__ Item s_q[LEAN_THREADS / 32][QCAP];
     __shared__ __align__(16) uint16_t s_stg[LEAN_THREADS / 32][2 * WARP_MERGE_MAX];
@@ -1654,7 +1657,7 @@ uint64_t heavy_warps(const rb_plan *p, const rb_schedule &sc) {
 // warps of the k_lean launch for this plan and schedule
 uint64_t lean_warps(const rb_plan *p, const rb_schedule &sc) {
     const unsigned long long lean_cap =
-        (unsigned long long)sm_count() * (sc.lean_ctas_per_sm ? sc.lean_ctas_per_sm : 8) * (LEAN_THREADS / 32);
+        (unsigned long long)sm_count() * (sc.lean_ctas_per_sm ? sc.lean_ctas_per_sm : LEAN_CTAS_MAX) * (LEAN_THREADS / 32);
     const unsigned long long warps = std::min<unsigned long long>(p->total_tiles, lean_cap);
     return std::max<unsigned long long>(1, (warps + LEAN_THREADS / 32 - 1) / (LEAN_THREADS / 32)) *
            (LEAN_THREADS / 32);
@@ -1997,7 +2000,7 @@ rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *be
     const rb_schedule saved = current_schedule();
     static const uint32_t heavy[][2] = {{2, 6}, {4, 3}, {8, 1}};
     static const uint32_t smalls[] = {64, 256, 512};
-    static const uint32_t leans[] = {4, 8};
+    static const uint32_t leans[] = {4, 7};
     rb_schedule win = saved;
     double win_ms = 1e30;
     std::vector<rb_t *> outs(p->q.size(), nullptr);
