@@ -229,7 +229,7 @@ void rb_plan_free(rb_plan_t *p);
  * the largest array pair (values on both sides) that one lane of the lean
  * kernel merges alone (larger array pairs up to 1024 values are merged by the
  * whole warp; bitsets and larger containers are deferred to the heavy
- * kernel); the lean kernel's CTAs of 128 threads per SM (0 = 8); and how many
+ * kernel); the lean kernel's CTAs of 128 threads per SM (0 = 7, the most that fit); and how many
  * 128-byte lines of each queued container's payload the lean kernel hints
  * into L2 ahead of use (0 = none). */
 typedef struct {
@@ -256,6 +256,31 @@ rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *be
  * count-only evaluation.  k == 0 gives the empty set. */
 rb_status rb_multi_op(rb_op op, const rb_t *const *in, uint32_t k, rb_t **out, uint64_t *card,
                       void *stream);
+
+/* --------------------------------------------------------- accumulation */
+
+/* In-place accumulation acc = acc op b over a stream of bitmaps, op RB_OR or
+ * RB_AND (Sec. 5 "Wide unions": a union of many bitmaps computed partly in
+ * place; Sec. 2.2: lazy operations that skip the cardinality of
+ * intermediate results).  The accumulator holds one 8 KB bitset tile per
+ * key present; creation reserves a 65536-entry key map and max_keys tiles
+ * (max_keys * 8 KB + 2 MB of device memory, from the installed allocator),
+ * and no later call allocates device memory except rb_accum_result's
+ * output.  rb_accum_add only enqueues work on `stream` (OR: each of b's
+ * containers is OR-ed into its key's tile, touching only the words it
+ * covers; AND: the first add fills the accumulator, later ones drop the keys
+ * b lacks and AND the rest).  Calls on one accumulator must be ordered (one
+ * stream, or synchronised).  If the keys added exceed max_keys, the adds
+ * skip the keys that find no tile and rb_accum_result returns RB_ERANGE.
+ * rb_accum_result canonicalises the current state into a new bitmap (out,
+ * may be NULL for the cardinality only) without changing the accumulator,
+ * and synchronises `stream`.  rb_accum_reset empties it. */
+typedef struct rb_accum rb_accum_t;
+rb_status rb_accum_create(rb_op op, uint32_t max_keys, void *stream, rb_accum_t **out);
+rb_status rb_accum_add(rb_accum_t *acc, const rb_t *b, void *stream);
+rb_status rb_accum_result(rb_accum_t *acc, rb_t **out, uint64_t *card, void *stream);
+rb_status rb_accum_reset(rb_accum_t *acc, void *stream);
+void rb_accum_free(rb_accum_t *acc);
 
 /* -------------------------------------------------------------- serving */
 

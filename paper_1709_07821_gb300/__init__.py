@@ -89,6 +89,10 @@ def _sig(L):
         "rb_contains_many": [vp, vp, u64, i32, vp, vp],
         "rb_contains": [vp, u32, ctypes.POINTER(i32)],
         "rb_serialize": [vp, vp, u64, pu64, vp],
+        "rb_accum_create": [i32, u32, vp, pvp],
+        "rb_accum_add": [vp, vp, vp],
+        "rb_accum_result": [vp, pvp, pu64, vp],
+        "rb_accum_reset": [vp, vp],
         "rb_deserialize": [vp, u64, vp, pvp],
         "rb_batch_op": [vp, u32, vp, u64, vp, vp, vp],
         "rb_batch_jaccard": [vp, u32, vp, vp, u64, vp, vp, vp, vp],
@@ -111,7 +115,7 @@ def _sig(L):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int
-    for name in ("rb_free", "rb_plan_free", "rb_server_destroy"):
+    for name in ("rb_free", "rb_plan_free", "rb_server_destroy", "rb_accum_free"):
         getattr(L, name).argtypes = [vp]
         getattr(L, name).restype = None
     L.rb_free_array.argtypes = [vp, u64]
@@ -501,6 +505,42 @@ def multi_op(op: int, inputs, count_only: bool = False, stream=None):
     _check(lib().rb_multi_op(op, _handles(inputs), len(inputs), None if count_only else ctypes.byref(h),
                              ctypes.byref(c), _stream(stream)))
     return (None if count_only else Bitmap(h.value)), c.value
+
+
+class Accumulator:
+    """In-place accumulation acc = acc op b (op AND or OR) over many bitmaps,
+    with device memory reserved once (max_keys tiles of 8 KB)."""
+
+    def __init__(self, op: int, max_keys: int = 65536, stream=None):
+        h = ctypes.c_void_p()
+        _check(lib().rb_accum_create(op, max_keys, _stream(stream), ctypes.byref(h)))
+        self._h = h.value
+
+    def add(self, b: "Bitmap", stream=None):
+        _check(lib().rb_accum_add(self._h, b._h, _stream(stream)))
+        return self
+
+    def result(self, want_bitmap: bool = True, stream=None):
+        """(bitmap or None, cardinality) of the current state."""
+        h = ctypes.c_void_p()
+        c = ctypes.c_uint64()
+        _check(lib().rb_accum_result(self._h, ctypes.byref(h) if want_bitmap else None, ctypes.byref(c),
+                                     _stream(stream)))
+        return (Bitmap(h.value) if h.value else None), c.value
+
+    def reset(self, stream=None):
+        _check(lib().rb_accum_reset(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rb_accum_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

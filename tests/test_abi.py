@@ -108,3 +108,13 @@ def test_deserialize_rejects_bad_images_without_gpu(librb, oracle_mod):
     data = image_from_layout(lay2)
     out = ctypes.c_void_p()
     assert librb.rb_deserialize(data, len(data), None, ctypes.byref(out)) == 1
+
+
+def test_accumulator_argument_checks_without_gpu(librb):
+    librb.rb_accum_create.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    assert librb.rb_accum_create(3, 100, None, ctypes.byref(out)) == 1       # XOR does not accumulate
+    assert librb.rb_accum_create(1, 0, None, ctypes.byref(out)) == 1         # no tiles
+    assert librb.rb_accum_create(1, 65537, None, ctypes.byref(out)) == 1     # more tiles than keys
+    assert librb.rb_accum_create(1, 10, None, None) == 1
+    assert out.value is None
