@@ -49,14 +49,19 @@ def measured_peaks():
 
 
 def kernel_source_sha256():
-    """SHA-256 of the pairwise kernels' sources without their comment-only
-    lines (csrc/rb_pairs.cu, rb_device.cuh, rb_internal.h, in that order)."""
+    """SHA-256 of the device code of the pairwise kernels without comment-only
+    lines: csrc/rb_pairs.cu and csrc/rb_internal.h up to their "host side"
+    marker line, and csrc/rb_device.cuh, in that order.  Host-only edits
+    leave it unchanged."""
     import hashlib
     h = hashlib.sha256()
     for f in ("rb_pairs.cu", "rb_device.cuh", "rb_internal.h"):
         with open(os.path.join(ROOT, "paper_1709_07821_gb300", "csrc", f)) as fh:
             for line in fh:
-                if not line.strip().startswith("//"):
+                t = line.strip()
+                if t.startswith("//") and t.endswith("host side"):
+                    break
+                if not t.startswith("//"):
                     h.update(line.encode())
     return h.hexdigest()
 
