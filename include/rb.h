@@ -205,6 +205,16 @@ typedef struct rb_plan rb_plan_t;
 rb_status rb_plan_create(const rb_t *const *pool, uint32_t pool_n, const rb_query *q, uint64_t nq,
                          void *stream, rb_plan_t **out);
 rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream);
+/* rb_plan_run in two halves, so that the host can prepare or consume other
+ * work while the device runs: rb_plan_launch enqueues a run (a graph replay
+ * on the plan's own stream, ordered after the work already on `stream`, and
+ * `stream` ordered after it) and returns at once; rb_plan_collect waits for
+ * it, reruns it with exact sizes if its output space ran out, and fills outs
+ * and counts as rb_plan_run does.  One run per plan may be outstanding
+ * (RB_EINVAL otherwise, and for a collect without a launch); several plans
+ * launched on one stream run one after another on the device. */
+rb_status rb_plan_launch(rb_plan_t *p, void *stream);
+rb_status rb_plan_collect(rb_plan_t *p, rb_t **outs, uint64_t *counts);
 /* Measurements of the last run, from CUDA events on the stream the kernels
  * ran on: the container-pair stage is a lean kernel (key merge, small pairs)
  * then a heavy kernel (pairs deferred by the lean one: bitsets, many values

@@ -98,6 +98,8 @@ def _sig(L):
         "rb_batch_jaccard": [vp, u32, vp, vp, u64, vp, vp, vp, vp],
         "rb_plan_create": [vp, u32, vp, u64, vp, pvp],
         "rb_plan_run": [vp, vp, vp, vp],
+        "rb_plan_launch": [vp, vp],
+        "rb_plan_collect": [vp, vp, vp],
         "rb_plan_stats": [vp, ctypes.POINTER(PlanTiming)],
         "rb_set_schedule": [ctypes.POINTER(Schedule)],
         "rb_get_schedule": [ctypes.POINTER(Schedule)],
@@ -409,6 +411,22 @@ class Plan:
         outs = (ctypes.c_void_p * max(1, self.n))()
         counts = np.zeros(self.n, np.uint64)
         _check(lib().rb_plan_run(self._h, outs, counts.ctypes.data if self.n else None, _stream(stream)))
+        if raw:
+            return outs, counts
+        if not want_bitmaps:
+            lib().rb_free_array(outs, self.n)
+            return None, counts
+        return [Bitmap(outs[i]) if outs[i] else None for i in range(self.n)], counts
+
+    def launch(self, stream=None):
+        """Enqueue a run and return at once (collect() finishes it)."""
+        _check(lib().rb_plan_launch(self._h, _stream(stream)))
+
+    def collect(self, want_bitmaps=True, raw=False):
+        """Wait for the launched run; results as run() returns them."""
+        outs = (ctypes.c_void_p * max(1, self.n))()
+        counts = np.zeros(self.n, np.uint64)
+        _check(lib().rb_plan_collect(self._h, outs, counts.ctypes.data if self.n else None))
         if raw:
             return outs, counts
         if not want_bitmaps:

@@ -108,8 +108,9 @@ void arena_ref(RbArena *a) {
 void budget_unref(RbBudget *b) {
     if (b && b->refs.fetch_sub(1) == 1) delete b;
 }
-void arena_unref(RbArena *a) {
-    if (a && a->refs.fetch_sub(1) == 1) {
+void arena_unref(RbArena *a) { arena_unref_n(a, 1); }
+void arena_unref_n(RbArena *a, int n) {
+    if (a && n > 0 && a->refs.fetch_sub(n) == n) {
         if (a->native) dev_free_native(a->ptr, a->stream);
         else dev_free(a->ptr, a->bytes, a->stream);
         if (a->budget) {
@@ -487,15 +488,43 @@ rb_status rb_get_schedule(rb_schedule *s) {
     return RB_OK;
 }
 
+static void block_unref(RbBlock *k, uint64_t n) {
+    if (k->refs.fetch_sub(n) == n) {
+        delete[] k->items;
+        delete k;
+    }
+}
+
 void rb_free(rb_t *b) {
     if (!b) return;
     arena_unref(b->arena);
-    delete b;
+    if (b->block) block_unref(b->block, 1);
+    else delete b;
 }
 
 void rb_free_array(rb_t *const *hs, uint64_t n) {
     if (!hs) return;
-    for (uint64_t i = 0; i < n; i++) rb_free(hs[i]);
+    // runs of handles that share an arena and a block (the results of one
+    // batch) give back their references in one step each
+    uint64_t i = 0;
+    while (i < n) {
+        rb *h = hs[i];
+        if (!h) { i++; continue; }
+        if (!h->block) { rb_free(h); i++; continue; }
+        RbArena *a = h->arena;
+        RbBlock *k = h->block;
+        uint64_t j = i + 1;
+        while (j < n && hs[j] && hs[j]->block == k && hs[j]->arena == a) j++;
+        // the run holds j - i references of each; the block is released last
+        uint64_t left = j - i;
+        while (left) {
+            const int step = (int)std::min<uint64_t>(left, 1u << 30);
+            arena_unref_n(a, step);
+            left -= (uint64_t)step;
+        }
+        block_unref(k, j - i);
+        i = j;
+    }
 }
 
 rb_status rb_cardinality(const rb_t *b, uint64_t *out) {

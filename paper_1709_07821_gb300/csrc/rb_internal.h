@@ -85,6 +85,8 @@ struct RbArena {
     uint64_t charge;
 };
 
+struct RbBlock;
+
 struct rb {
     uint32_t n;            // containers
     uint64_t card;         // total cardinality
@@ -94,6 +96,14 @@ struct rb {
     uint64_t *descs;       // device
     uint8_t *base;         // device: descriptor offsets are relative to this
     RbArena *arena;        // owner of keys/descs/payload memory (may be shared)
+    RbBlock *block;        // handles of one batch are allocated together (NULL: alone)
+};
+
+// the handles of one batch's results, allocated as one array and released
+// when the last of them is freed
+struct RbBlock {
+    std::atomic<uint64_t> refs;
+    rb *items;
 };
 
 namespace rbi {
@@ -117,6 +127,7 @@ void dev_free_native(void *p, cudaStream_t s);
 void budget_unref(RbBudget *b);
 void arena_ref(RbArena *a);
 void arena_unref(RbArena *a);
+void arena_unref_n(RbArena *a, int n);   // n references at once
 
 // pinned host staging buffer of the calling thread (grows; never shrinks)
 void *pinned_scratch(uint64_t bytes);

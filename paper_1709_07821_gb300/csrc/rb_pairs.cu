@@ -1487,7 +1487,10 @@ struct rb_plan {
     PairStats *h_stats = nullptr;
     ExecState *h_es = nullptr;
     cudaStream_t ps = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev_in = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev_in = nullptr, ev_done = nullptr;
+    RbArena *pending = nullptr;   // result memory of a run launched by rb_plan_launch, not yet collected
+    bool pending_graph = false;
+    cudaStream_t pending_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     rb_schedule gsched = {0, 0, 0, 0, 0};
     double last_ms = 0, last_lean_ms = 0, last_heavy_ms = 0;
@@ -1508,6 +1511,11 @@ void plan_destroy(rb_plan *p) {
     if (p->ev1) cudaEventDestroy(p->ev1);
     if (p->ev2) cudaEventDestroy(p->ev2);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_done) cudaEventDestroy(p->ev_done);
+    if (p->pending) {
+        if (p->ps) cudaStreamSynchronize(p->ps);
+        arena_unref(p->pending);
+    }
     if (p->ps) cudaStreamDestroy(p->ps);
     delete p;
 }
@@ -1637,6 +1645,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev2);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         plan_destroy(p);
         return cuda_err(e, "plan setup");
@@ -1727,11 +1736,11 @@ ArenaLayout arena_layout(const rb_plan *p) {
     return L;
 }
 
-// one run with the plan's current caps; on success *arena holds the results;
-// *overflow tells the caller to retry with the exact sizes now recorded
-rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool *overflow) {
+// Enqueue one run with the plan's current caps: as a graph replay on the
+// plan's own stream, ordered after the work already on s and with s ordered
+// after it, or directly on s.  *arena receives the result memory.
+rb_status run_launch(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena) {
     *arena = nullptr;
-    *overflow = false;
     const rb_schedule sc = current_schedule();
     const ArenaLayout L = arena_layout(p);
     if (L.bytes >= MAX_OFFSET)
@@ -1772,11 +1781,27 @@ rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_in, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->ps, p->ev_in, 0);
         if (e == cudaSuccess) e = cudaGraphLaunch(p->gexec, p->ps);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(p->ps);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_done, p->ps);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_done, 0);
     } else {
         e = enqueue_run(p, sc, s, false);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
+    if (e != cudaSuccess) {
+        arena_unref(a);
+        return cuda_err(e, "batch run");
+    }
+    *arena = a;
+    return RB_OK;
+}
+
+// Wait for a launched run and check it.  On success *arena holds the
+// results; *overflow tells the caller to retry with the exact sizes now
+// recorded (the run's memory is then released).
+rb_status run_wait(rb_plan *p, cudaStream_t s, bool graph, RbArena *a, RbArena **arena, bool *overflow) {
+    *arena = nullptr;
+    *overflow = false;
+    ExecState &h = *p->h_es;
+    cudaError_t e = cudaStreamSynchronize(graph ? p->ps : s);
     if (e != cudaSuccess) {
         arena_unref(a);
         return cuda_err(e, "batch run");
@@ -1816,20 +1841,54 @@ rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool
     return RB_OK;
 }
 
-rb_status plan_execute(rb_plan *p, rb_t **outs, uint64_t *counts, cudaStream_t s, bool graph) {
-    clear_stale_error();
+rb_status run_once(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena, bool *overflow) {
+    RbArena *a = nullptr;
+    rb_status st = run_launch(p, s, graph, &a);
+    if (st != RB_OK) return st;
+    return run_wait(p, s, graph, a, arena, overflow);
+}
+
+rb_status finish_results(rb_plan *p, RbArena *a, rb_t **outs, uint64_t *counts);
+
+// a launched run (first) collected, retried synchronously with the exact
+// sizes while the arena overflowed, then turned into results
+rb_status plan_complete(rb_plan *p, RbArena *first, rb_t **outs, uint64_t *counts, cudaStream_t s, bool graph) {
     RbArena *a = nullptr;
     bool overflow = false;
-    rb_status st = RB_OK;
-    for (int attempt = 0; attempt < 3; attempt++) {
-        st = run_once(p, s, attempt == 0 ? graph : false, &a, &overflow);
-        if (st != RB_OK) return st;
-        if (!overflow) break;
-    }
+    rb_status st = run_wait(p, s, graph, first, &a, &overflow);
+    for (int attempt = 1; st == RB_OK && overflow && attempt < 3; attempt++) st = run_once(p, s, false, &a, &overflow);
+    if (st != RB_OK) return st;
     if (overflow) return set_err(RB_ENOMEM, "batch: output arena overflow persisted");
+    return finish_results(p, a, outs, counts);
+}
+
+rb_status plan_execute(rb_plan *p, rb_t **outs, uint64_t *counts, cudaStream_t s, bool graph) {
+    clear_stale_error();
+    RbArena *first = nullptr;
+    rb_status st = run_launch(p, s, graph, &first);
+    if (st != RB_OK) return st;
+    return plan_complete(p, first, outs, counts, s, graph);
+}
+
+// result handles and counts of a completed run whose memory is a
+rb_status finish_results(rb_plan *p, RbArena *a, rb_t **outs, uint64_t *counts) {
     const uint64_t nq = p->q.size();
     const ArenaLayout L = arena_layout(p);
     uint64_t alg = 0, outb = 0;
+    // the result handles share one allocation and take their arena
+    // references in one step
+    RbBlock *blk = nullptr;
+    uint64_t nm = 0;
+    if (outs) {
+        for (uint64_t i = 0; i < nq; i++) nm += (p->pairs[i].flags & F_COUNT) ? 0 : 1;
+        if (nm) {
+            blk = new RbBlock;
+            blk->items = new rb[nm]();
+            blk->refs.store(nm);
+            a->refs.fetch_add((int)nm);
+        }
+    }
+    uint64_t used = 0;
     for (uint64_t i = 0; i < nq; i++) {
         const PairDev &d = p->pairs[i];
         const PairStats &S = p->h_stats[i];
@@ -1850,7 +1909,7 @@ rb_status plan_execute(rb_plan *p, rb_t **outs, uint64_t *counts, cudaStream_t s
         outb += S.words + 8192ull * S.nbits + 10ull * S.n_out;
         if (counts) counts[i] = S.card;
         if (outs) {
-            rb *h = handle_new();
+            rb *h = &blk->items[used++];
             h->n = S.n_out;
             h->card = S.card;
             h->word_bytes = S.words;
@@ -1859,7 +1918,7 @@ rb_status plan_execute(rb_plan *p, rb_t **outs, uint64_t *counts, cudaStream_t s
             h->descs = (uint64_t *)a->ptr + d.pos_base;
             h->keys = (uint16_t *)((uint8_t *)a->ptr + L.o_keys) + d.pos_base;
             h->arena = a;
-            arena_ref(a);
+            h->block = blk;
             outs[i] = h;
         }
     }
@@ -1977,6 +2036,34 @@ rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream)
     if (p->any_mat && !outs) return set_err(RB_EINVAL, "rb_plan_run: outs is NULL but the plan materialises");
     // the first run sizes the arena exactly; later runs replay a CUDA graph
     return plan_execute(p, outs, counts, (cudaStream_t)stream, p->exact);
+}
+
+rb_status rb_plan_launch(rb_plan_t *p, void *stream) {
+    if (!p) return set_err(RB_EINVAL, "rb_plan_launch: NULL plan");
+    if (p->pending) return set_err(RB_EINVAL, "rb_plan_launch: the previous run has not been collected");
+    clear_stale_error();
+    RbArena *a = nullptr;
+    rb_status st = run_launch(p, (cudaStream_t)stream, p->exact, &a);
+    if (st != RB_OK) return st;
+    p->pending = a;
+    p->pending_graph = p->exact;
+    p->pending_stream = (cudaStream_t)stream;
+    return RB_OK;
+}
+
+rb_status rb_plan_collect(rb_plan_t *p, rb_t **outs, uint64_t *counts) {
+    if (!p) return set_err(RB_EINVAL, "rb_plan_collect: NULL plan");
+    if (!p->pending) return set_err(RB_EINVAL, "rb_plan_collect: no run was launched");
+    if (outs)
+        for (uint64_t i = 0; i < p->q.size(); i++) outs[i] = nullptr;
+    RbArena *a = p->pending;
+    p->pending = nullptr;
+    if (p->any_mat && !outs) {
+        // the run still has to finish before its memory goes back
+        plan_complete(p, a, nullptr, nullptr, p->pending_stream, p->pending_graph);
+        return set_err(RB_EINVAL, "rb_plan_collect: outs is NULL but the plan materialises");
+    }
+    return plan_complete(p, a, outs, counts, p->pending_stream, p->pending_graph);
 }
 
 rb_status rb_plan_stats(const rb_plan_t *p, rb_plan_timing *t) {

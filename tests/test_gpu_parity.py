@@ -333,3 +333,31 @@ def fig1_like():
                            np.arange(2**16 + 300, 2**16 + 400)]).astype(np.uint32)
     evens = np.arange(2 * 2**16, 3 * 2**16, 2, dtype=np.uint32)
     return np.concatenate([arr, runs, evens])
+
+
+def test_plan_launch_and_collect(rb, orc, workloads_mod):
+    """Two plans launched back to back on one stream and collected later give
+    the same results as synchronous runs and as the oracle."""
+    pool = _pool(workloads_mod, "batched", 24, 5.2, seed=71)
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    O = [orc.Bitmap.from_sorted(v) for v in vals]
+    ops, a, b = workloads_mod.pairs(7, 120, pool.n)
+    pm = rb.Plan(G, ops, a, b)
+    pj = rb.Plan(G, np.zeros(len(ops), np.uint32), a, b, np.full(len(ops), rb.Q_COUNT_ONLY, np.uint32))
+    ref, cref = pm.run()
+    _, jref = pj.run(want_bitmaps=False)
+    for rnd in range(3):              # the first launch sizes exactly, later ones replay graphs
+        pm.launch()
+        pj.launch()
+        with pytest.raises(rb.RoaringError):
+            pm.launch()                # one outstanding run per plan
+        got, c = pm.collect()
+        _, j = pj.collect(want_bitmaps=False)
+        assert np.array_equal(c, cref) and np.array_equal(j, jref)
+        for i in range(0, len(ops), 7):
+            assert_layout_eq(got[i].layout(), ref[i].layout(), f"round {rnd} pair {i}")
+            assert_layout_eq(got[i].layout(), O[a[i]].op(int(ops[i]), O[b[i]]).layout(), f"oracle {i}")
+            assert int(j[i]) == O[a[i]].op_card(0, O[b[i]])
+    with pytest.raises(rb.RoaringError):
+        pm.collect()                   # nothing launched
