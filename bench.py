@@ -492,8 +492,11 @@ def serving_leg(rb, G, sizes, rates=(1e3, 1e4, 1e5, 1e6), seconds=2.0, max_queri
     import workloads as W
     out = []
     srv = rb.Server(G, mem_budget=64 << 30, max_inflight_batches=4, max_batch=256)
+    import gc
     switch = sys.getswitchinterval()
     sys.setswitchinterval(5e-5)   # the two client threads hand the interpreter over quickly
+    gc.collect()
+    gc.disable()                  # no collector pause stalls the frontend thread
     try:
         for rate in rates:
             n = int(min(max_queries, max(200, rate * seconds)))
@@ -542,6 +545,7 @@ def serving_leg(rb, G, sizes, rates=(1e3, 1e4, 1e5, 1e6), seconds=2.0, max_queri
                         "submit_lateness_p99_ms": float(np.percentile(late, 99)) * 1e3})
         st = srv.stats()
     finally:
+        gc.enable()
         sys.setswitchinterval(switch)
         srv.close()
     return {"loads": out, "batches": st["batches"], "peak_inflight": st["peak_inflight"],

@@ -418,11 +418,34 @@ __device__ __noinline__ void copy_tile(ExecState *es, unsigned long long *wa, un
         const uint32_t ex = __shfl_sync(FULL, wincl - nw, j);
         return g < T ? __ldg(S + (g - ex)) : 0u;
     };
-    // 128 words per round, 4 loads per lane in flight; the first round is
-    // read before the allocation returns
+    // the first round is read before the allocation returns; one contiguous
+    // source moves 256 words per round (8 loads per lane in flight), a
+    // gathered one 128 (4 loads, each after its container search)
     unsigned long long wbase = 0;
     bool ok = true;
     uint32_t *D = nullptr;
+    if (one) {
+        for (uint32_t g0 = 0;; g0 += 32 * 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t g = g0 + 32u * k + lane;
+                v[k] = g < T ? __ldg(S1 + g) : 0u;
+            }
+            if (g0 == 0) {
+                wbase = lean_alloc(es, wa, total, lane);
+                ok = wbase != ALLOC_FAIL;
+                if (!ok) break;
+                D = reinterpret_cast<uint32_t *>(es->arena + es->words_off + wbase);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t g = g0 + 32u * k + lane;
+                if (g < T) D[g] = v[k];
+            }
+            if (g0 + 32 * 8 >= T) break;
+        }
+    } else
     for (uint32_t g0 = 0;; g0 += 128) {
         uint32_t v[4];
 #pragma unroll
