@@ -331,9 +331,12 @@ __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *
     uint32_t i = 0, j = 0, pa = 0xFFFFFFFFu, last = 0xFFFFFFFEu;
     c = 0;
     r = 0;
-    const bool keep_b = (tbl & 1u) != 0;   // AND/ANDNOT stop once a is exhausted
+    // once one input is exhausted the rest of the other is kept whole or
+    // dropped whole: AND stops at the first end, ANDNOT once a ends, OR and
+    // XOR run to both ends
+    const bool keep_a_rest = (tbl & 4u) != 0, keep_b_rest = (tbl & 1u) != 0;
 #pragma unroll 1
-    while (i < na || (keep_b && j < nb)) {
+    while ((i < na && (j < nb || keep_a_rest)) || (j < nb && keep_b_rest)) {
         const uint32_t va = i < na ? (uint32_t)__ldg(a + i) : KEY_END;
         const uint32_t vb = j < nb ? (uint32_t)__ldg(b + j) : KEY_END;
         const bool ta = va <= vb;
