@@ -91,6 +91,9 @@ void budget_notify(void *ctx) { ((rb_server *)ctx)->cv_work.notify_all(); }
 void retire(rb_server *S, Flight *f) {
     std::vector<rb_t *> outs(f->tickets.size(), nullptr);
     std::vector<uint64_t> cards(f->tickets.size(), 0);
+    // the batch's device work is complete; its results may outlive the loop
+    // and its streams, so their memory is released on the default stream
+    if (f->arena) f->arena->stream = nullptr;
     rb_status st = multi_finish(f->mb, f->arena, outs.data(), cards.data());
     for (size_t i = 0; i < f->tickets.size(); i++) {
         auto it = S->reqs.find(f->tickets[i]);

@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def full(oracle_mod, workloads_mod):
+    """The full-size pool on the device with both plans run as bench.py runs them."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -33,7 +34,7 @@ def full(oracle_mod, workloads_mod):
     plan_j.run(want_bitmaps=False)
     outs, counts = plan_m.run()           # graph replay, as timed by bench.py
     _, inter = plan_j.run(want_bitmaps=False)
-    yield rb, pool, ops, a, b, outs, counts, inter
+    yield rb, pool, ops, a, b, outs, counts, inter, G
     for o in outs:
         if o is not None:
             o.free()
@@ -42,7 +43,7 @@ def full(oracle_mod, workloads_mod):
 
 
 def test_every_cardinality_matches_the_count_identities(full):
-    rb, pool, ops, a, b, outs, counts, inter = full
+    rb, pool, ops, a, b, outs, counts, inter, _ = full
     sz = pool.sizes().astype(np.int64)
     A, B, I = sz[a], sz[b], inter.astype(np.int64)
     want = np.select([ops == 0, ops == 1, ops == 2, ops == 3], [I, A + B - I, A - I, A + B - 2 * I])
@@ -56,7 +57,7 @@ def test_every_cardinality_matches_the_count_identities(full):
 
 
 def test_sampled_outputs_match_the_oracle(full, oracle_mod):
-    rb, pool, ops, a, b, outs, counts, inter = full
+    rb, pool, ops, a, b, outs, counts, inter, _ = full
     rng = np.random.default_rng(2024)
     cls = np.array([pool.klass(i) for i in range(pool.n)])
     pick = []
@@ -84,3 +85,55 @@ def test_sampled_outputs_match_the_oracle(full, oracle_mod):
         want = exp.layout()
         for k in ("keys", "types", "cards", "offs", "payload"):
             assert np.array_equal(got[k], want[k]), (i, int(ops[i]), k)
+
+
+def test_serving_at_full_size(full, oracle_mod, workloads_mod):
+    """The serving loop over the full-size pool as its index, in the
+    configuration bench.py times (64 GB budget, 4 batches in flight, up to 256
+    queries each, bulk submission and polling): every result equals the same
+    query run alone, and a stratified sample equals the oracle's fold."""
+    rb, pool, ops, a, b, outs, counts, inter, G = full
+    mops, ks, co, mem = workloads_mod.multi_queries(5, 300, pool.n)
+    srv = rb.Server(G, mem_budget=64 << 30, max_inflight_batches=4, max_batch=256)
+    try:
+        tickets = srv.submit_many(mops, ks, co, mem)
+        res = {}
+        while len(res) < len(mops):
+            t, st, cards, _, bms = srv.poll(cap=512, timeout_ms=120000, want_bitmaps=True)
+            assert len(t) > 0 and np.all(st == 0)
+            for x, c, bm in zip(t, cards, bms):
+                res[int(x)] = (int(c), bm)
+    finally:
+        srv.close()
+    rng = np.random.default_rng(7)
+    sample = set()
+    for op in (0, 1):
+        for c in (0, 1):
+            idx = np.nonzero((mops == op) & (co == c))[0]
+            sample.update(int(i) for i in rng.choice(idx, size=min(3, len(idx)), replace=False))
+    orc = {}
+    for q in range(len(mops)):
+        card, bm = res[int(tickets[q])]
+        members = [G[m] for m in mem[q, :ks[q]]]
+        alone, card_alone = rb.multi_op(int(mops[q]), members, count_only=bool(co[q]))
+        assert card == card_alone, q
+        if co[q]:
+            assert bm is None
+        else:
+            got, ref = bm.layout(), alone.layout()
+            for k in ("keys", "types", "cards", "offs", "payload"):
+                assert np.array_equal(got[k], ref[k]), (q, k)
+        if q in sample:
+            for m in mem[q, :ks[q]]:
+                if int(m) not in orc:
+                    orc[int(m)] = oracle_mod.Bitmap.from_sorted(pool.values(int(m)))
+            exp = oracle_mod.Bitmap.multi(int(mops[q]), [orc[int(m)] for m in mem[q, :ks[q]]])
+            assert card == exp.card, q
+            if not co[q]:
+                want = exp.layout()
+                for k in ("keys", "types", "cards", "offs", "payload"):
+                    assert np.array_equal(bm.layout()[k], want[k]), (q, k)
+        if bm is not None:
+            bm.free()
+        if alone is not None:
+            alone.free()

@@ -159,3 +159,26 @@ def test_bulk_submit_and_poll(env):
             srv.submit_many([rb.XOR], [2], [0], np.zeros((1, 8), np.uint32))
     finally:
         srv.close()
+
+
+def test_results_outlive_the_server(env):
+    """Result bitmaps stay valid and freeable after the serving loop (and its
+    streams) are gone."""
+    rb, orc, W, pool, G, O = env
+    ops, ks, co, mem = W.multi_queries(54, 24, pool.n)
+    srv = rb.Server(G, mem_budget=8 << 30, max_inflight_batches=3, max_batch=8)
+    kept = []
+    try:
+        tickets = srv.submit_many(ops, ks, np.zeros(len(ops), np.uint32), mem)
+        for q, t in enumerate(tickets):
+            bm, card, _ = srv.wait(int(t), timeout_ms=60000)
+            kept.append((q, bm, card))
+    finally:
+        srv.close()
+    for q, bm, card in kept:
+        exp = orc.Bitmap.multi(int(ops[q]), [O[m] for m in mem[q, :ks[q]]])
+        assert card == exp.card
+        lay, ref = bm.layout(), exp.layout()
+        for k in ("keys", "types", "cards", "offs", "payload"):
+            assert np.array_equal(lay[k], ref[k]), (q, k)
+        bm.free()
