@@ -126,8 +126,12 @@ class Clocks:
     """nvidia-smi sampling during the timed region."""
 
     def __init__(self, gpu_index: int):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        import tempfile
+        # raw samples go to a scratch file (RB_BENCH_CLOCKS_DIR if set); the
+        # JSON line carries their summary
+        d = os.environ.get("RB_BENCH_CLOCKS_DIR") or tempfile.gettempdir()
+        os.makedirs(d, exist_ok=True)
+        self.path = os.path.join(d, f"rb_bench_clocks_gpu{gpu_index}_{os.getpid()}.csv")
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")

@@ -81,9 +81,16 @@ struct ExecState {
     unsigned int status, pad;
 };
 
+// both input views of a query, so that a kernel reads them without first
+// reading the query's pool indexes
+struct QViews {
+    BmView a, b;
+};
+
 struct PairParams {
     const BmView *pool;
     const PairDev *pairs;
+    const QViews *qv;
     const unsigned long long *tile_base;
     PairStats *stats;
     ExecState *es;
@@ -521,7 +528,7 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
     }
     const uint32_t p = cur.p;
     const PairDev pd = P.pairs[p];
-    const BmView A = P.pool[pd.a], B = P.pool[pd.b];
+    const BmView A = P.qv[p].a, B = P.qv[p].b;
     ExecState *es = P.es;
     const uint32_t op = pd.op;
     const bool count_only = (pd.flags & F_COUNT) != 0;
@@ -1064,7 +1071,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     const uint32_t mode = has ? (it.info >> 20) & 7u : M_NONE;
     const uint32_t key = it.info & 0xFFFFu;
     const PairDev pd = P.pairs[it.p];
-    const uint8_t *abase = P.pool[pd.a].base, *bbase = P.pool[pd.b].base;
+    const uint8_t *abase = P.qv[it.p].a.base, *bbase = P.qv[it.p].b.base;
     const bool count = (pd.flags & F_COUNT) != 0;
     const uint32_t op = count ? (uint32_t)OP_AND : pd.op;
     const uint32_t tbl = keep_table(op);
@@ -1393,7 +1400,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
         const Deferred D = Dn;
         en = next(Dn);
         const PairDev pd = P.pairs[D.p];
-        const BmView A = P.pool[pd.a], B = P.pool[pd.b];
+        const BmView A = P.qv[D.p].a, B = P.qv[D.p].b;
         const uint32_t kind = D.kind_key >> 16, key = D.kind_key & 0xFFFFu;
         PairStats *S = P.stats + D.p;
         if (pd.flags & F_COUNT) {
@@ -1507,6 +1514,7 @@ struct rb_plan {
     uint64_t tables_bytes = 0;
     BmView *d_pool = nullptr;
     PairDev *d_pairs = nullptr;
+    QViews *d_qv = nullptr;
     unsigned long long *d_tile_base = nullptr;
     PairStats *d_stats = nullptr;
     ExecState *d_es = nullptr;
@@ -1647,7 +1655,8 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     // device tables: pool views | pairs | tile prefix | stats | exec state
     const uint64_t o_pool = 0;
     const uint64_t o_pairs = align_up(o_pool + sizeof(BmView) * (uint64_t)pool_n, 256);
-    const uint64_t o_tb = align_up(o_pairs + sizeof(PairDev) * nq, 256);
+    const uint64_t o_qv = align_up(o_pairs + sizeof(PairDev) * nq, 256);
+    const uint64_t o_tb = align_up(o_qv + sizeof(QViews) * nq, 256);
     const uint64_t o_stats = align_up(o_tb + 8ull * (nq + 1), 256);
     const uint64_t o_es = align_up(o_stats + sizeof(PairStats) * nq, 256);
     p->tables_bytes = o_es + 256;
@@ -1655,6 +1664,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     if (!p->tables) { plan_destroy(p); return RB_ENOMEM; }
     p->d_pool = (BmView *)(p->tables + o_pool);
     p->d_pairs = (PairDev *)(p->tables + o_pairs);
+    p->d_qv = (QViews *)(p->tables + o_qv);
     p->d_tile_base = (unsigned long long *)(p->tables + o_tb);
     p->d_stats = (PairStats *)(p->tables + o_stats);
     p->d_es = (ExecState *)(p->tables + o_es);
@@ -1662,6 +1672,8 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     BmView *hv = (BmView *)(hbuf.data() + o_pool);
     for (uint32_t i = 0; i < pool_n; i++) hv[i] = view_of(pool[i]);
     if (nq) memcpy(hbuf.data() + o_pairs, p->pairs.data(), sizeof(PairDev) * nq);
+    QViews *hq = (QViews *)(hbuf.data() + o_qv);
+    for (uint64_t i = 0; i < nq; i++) hq[i] = {hv[p->pairs[i].a], hv[p->pairs[i].b]};
     memcpy(hbuf.data() + o_tb, tb.data(), 8ull * (nq + 1));
     cudaError_t e = cudaMallocHost((void **)&p->h_stats, sizeof(PairStats) * std::max<uint64_t>(nq, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&p->h_es, sizeof(ExecState));
@@ -1707,6 +1719,7 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     PairParams P;
     P.pool = p->d_pool;
     P.pairs = p->d_pairs;
+    P.qv = p->d_qv;
     P.tile_base = p->d_tile_base;
     P.stats = p->d_stats;
     P.es = p->d_es;
