@@ -368,16 +368,25 @@ def _queries(ops, a, b, flags=None):
     return q
 
 
-def batch_op(pool, ops, a, b, flags=None, stream=None):
+def batch_op(pool, ops, a, b, flags=None, stream=None, raw=False):
     """Run len(ops) pairwise queries over `pool` in one launch.  Returns
-    (bitmaps, counts): bitmaps[i] is None for count-only queries."""
+    (bitmaps, counts): bitmaps[i] is None for count-only queries.  With
+    raw=True the results stay a ctypes array of library handles (no Python
+    object per result); release them with free_handles."""
     n = len(ops)
     q = _queries(ops, a, b, flags)
     outs = (ctypes.c_void_p * max(1, n))()
     counts = np.zeros(n, np.uint64)
     _check(lib().rb_batch_op(_handles(pool), len(pool), q, n, outs, counts.ctypes.data if n else None,
                              _stream(stream)))
+    if raw:
+        return outs, counts
     return [Bitmap(outs[i]) if outs[i] else None for i in range(n)], counts
+
+
+def free_handles(outs, n: int):
+    """Release n raw result handles (from batch_op(raw=True)) in one call."""
+    lib().rb_free_array(outs, n)
 
 
 def batch_jaccard(pool, a, b, stream=None):

@@ -192,6 +192,19 @@ def test_batch_matches_oracle_and_per_pair(rb, orc, workloads_mod, name, n, hi):
     for i in range(0, len(a), 7):
         oj, oi, ou = O[a[i]].jaccard(O[b[i]])
         assert (ii[i], uu[i]) == (oi, ou) and j[i] == oj
+    # the same batch with raw handles, released in one call
+    raw, c2 = rb.batch_op(G, ops, a, b, flags, raw=True)
+    assert np.array_equal(c2, counts)
+    for i in range(0, len(ops), 9):
+        if flags[i]:
+            assert not raw[i]
+            continue
+        view = rb.Bitmap(raw[i])
+        try:
+            assert_layout_eq(view.layout(), outs[i].layout(), f"raw {i}")
+        finally:
+            view._h = None          # the raw array still owns the handle
+    rb.free_handles(raw, len(ops))
 
 
 def test_plan_graph_replay(rb, orc, workloads_mod):
