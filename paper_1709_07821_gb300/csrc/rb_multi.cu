@@ -118,7 +118,7 @@ __device__ uint64_t alloc_b(MState *es, uint32_t lane) {
 // the others), in lane-private columns of the two tiles; the other keys are
 // folded by the whole warp in the tiles, as the general path does.
 constexpr uint32_t MK = 8;
-constexpr uint32_t LCAP = 128;   // 4096 u16 per tile / 32 lanes
+constexpr uint32_t LCAP = 256;   // both tiles as 8192 u16 / 32 lanes
 constexpr uint32_t NOIX = 0xFFFFFFFFu;
 constexpr uint32_t MKEY_END = 0x10000u;
 
@@ -149,8 +149,8 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint64_t x, uint32_t n) {
     return b;
 }
 
-// element e of a lane's column in a tile used as 4096 u16 (conflict-light:
-// consecutive lanes share 4-byte words)
+// element e of a lane's column in the warp's two tiles used as 8192 u16
+// (conflict-light: consecutive lanes share 4-byte words)
 __device__ __forceinline__ uint16_t &col(uint64_t *T, uint32_t e, uint32_t lane) {
     return reinterpret_cast<uint16_t *>(T)[e * 32 + lane];
 }
@@ -505,8 +505,8 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
         es->keys[qd.slot_base + pos] = (uint16_t)key;
     }
     if (empty) in_acc = 0;   // an absent container ends the key's AND: nothing is read
-    // lane path: the key's result in the lane's column of T0 or T1
-    uint64_t *X = T0, *Y = T1;
+    // lane path: the key's result in the lane's column of the two tiles
+    uint64_t *X = T0;
     uint32_t n = 0;
     if (lane_path) {
         if (is_and) {
@@ -530,27 +530,37 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
                 n = m;
             }
         } else {
-            for (uint32_t i = 0; i < k; i++) {
-                const uint32_t j = MS->ix[i][lane];
-                if (j == NOIX) continue;
-                const BmView V = P.pool[mem[i]];
-                const uint64_t d = __ldg(V.descs + j);
-                const uint16_t *A = reinterpret_cast<const uint16_t *>(V.base + d_off(d));
-                const uint32_t na = d_card(d);
-                // Y = X u A, both sorted, duplicates once
-                uint32_t x = 0, y = 0, m = 0;
-                while (x < n || y < na) {
-                    const uint32_t vx = x < n ? (uint32_t)col(X, x, lane) : MKEY_END;
-                    const uint32_t va = y < na ? (uint32_t)__ldg(A + y) : MKEY_END;
-                    const uint32_t v = vx < va ? vx : va;
-                    col(Y, m++, lane) = (uint16_t)v;
-                    x += vx == v;
-                    y += va == v;
+            // one k-way merge of the key's sorted arrays, duplicates once: the
+            // members' heads stay in registers, each output value takes the
+            // smallest and advances every member that holds it
+            const uint16_t *ap[MK];
+            uint32_t len[MK], at[MK], head[MK];
+#pragma unroll
+            for (uint32_t i = 0; i < MK; i++) {
+                ap[i] = nullptr;
+                len[i] = at[i] = 0;
+                head[i] = MKEY_END;
+                const uint32_t j = i < k ? MS->ix[i][lane] : NOIX;
+                if (j != NOIX) {
+                    const BmView V = P.pool[mem[i]];
+                    const uint64_t d = __ldg(V.descs + j);
+                    ap[i] = reinterpret_cast<const uint16_t *>(V.base + d_off(d));
+                    len[i] = d_card(d);
+                    head[i] = __ldg(ap[i]);
                 }
-                n = m;
-                uint64_t *t = X;
-                X = Y;
-                Y = t;
+            }
+            for (;;) {
+                uint32_t v = MKEY_END;
+#pragma unroll
+                for (uint32_t i = 0; i < MK; i++) v = min(v, head[i]);
+                if (v == MKEY_END) break;
+                col(X, n++, lane) = (uint16_t)v;
+#pragma unroll
+                for (uint32_t i = 0; i < MK; i++)
+                    if (head[i] == v) {
+                        at[i]++;
+                        head[i] = at[i] < len[i] ? (uint32_t)__ldg(ap[i] + at[i]) : MKEY_END;
+                    }
             }
         }
     }
