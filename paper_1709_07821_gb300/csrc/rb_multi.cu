@@ -388,6 +388,46 @@ __device__ void multi_key_wide(const MParams &P, uint32_t q, const MultiDev &qd,
     __syncwarp();
 }
 
+// The union of the K members' sorted arrays for this lane's key (the
+// containers MS->ix names), written to the lane's column of X; the members'
+// heads stay in registers, each output value takes the smallest and advances
+// every member that holds it.  Returns the number of values.
+template <uint32_t K>
+__device__ __forceinline__ uint32_t kway_merge(const MParams &P, const uint32_t *mem, const MScratch *MS, uint64_t *X,
+                                               uint32_t lane) {
+    const uint16_t *ap[K];
+    uint32_t len[K], at[K], head[K];
+#pragma unroll
+    for (uint32_t i = 0; i < K; i++) {
+        ap[i] = nullptr;
+        len[i] = at[i] = 0;
+        head[i] = MKEY_END;
+        const uint32_t j = MS->ix[i][lane];
+        if (j != NOIX) {
+            const BmView V = P.pool[mem[i]];
+            const uint64_t d = __ldg(V.descs + j);
+            ap[i] = reinterpret_cast<const uint16_t *>(V.base + d_off(d));
+            len[i] = d_card(d);
+            head[i] = __ldg(ap[i]);
+        }
+    }
+    uint32_t n = 0;
+    for (;;) {
+        uint32_t v = MKEY_END;
+#pragma unroll
+        for (uint32_t i = 0; i < K; i++) v = min(v, head[i]);
+        if (v == MKEY_END) break;
+        col(X, n++, lane) = (uint16_t)v;
+#pragma unroll
+        for (uint32_t i = 0; i < K; i++)
+            if (head[i] == v) {
+                at[i]++;
+                head[i] = at[i] < len[i] ? (uint32_t)__ldg(ap[i] + at[i]) : MKEY_END;
+            }
+    }
+    return n;
+}
+
 __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd, uint32_t local, uint64_t *T0,
                                 uint64_t *T1, MScratch *MS, uint32_t lane) {
     const uint32_t *mem = P.members + qd.mbase;
@@ -530,37 +570,17 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
                 n = m;
             }
         } else {
-            // one k-way merge of the key's sorted arrays, duplicates once: the
-            // members' heads stay in registers, each output value takes the
-            // smallest and advances every member that holds it
-            const uint16_t *ap[MK];
-            uint32_t len[MK], at[MK], head[MK];
-#pragma unroll
-            for (uint32_t i = 0; i < MK; i++) {
-                ap[i] = nullptr;
-                len[i] = at[i] = 0;
-                head[i] = MKEY_END;
-                const uint32_t j = i < k ? MS->ix[i][lane] : NOIX;
-                if (j != NOIX) {
-                    const BmView V = P.pool[mem[i]];
-                    const uint64_t d = __ldg(V.descs + j);
-                    ap[i] = reinterpret_cast<const uint16_t *>(V.base + d_off(d));
-                    len[i] = d_card(d);
-                    head[i] = __ldg(ap[i]);
-                }
-            }
-            for (;;) {
-                uint32_t v = MKEY_END;
-#pragma unroll
-                for (uint32_t i = 0; i < MK; i++) v = min(v, head[i]);
-                if (v == MKEY_END) break;
-                col(X, n++, lane) = (uint16_t)v;
-#pragma unroll
-                for (uint32_t i = 0; i < MK; i++)
-                    if (head[i] == v) {
-                        at[i]++;
-                        head[i] = at[i] < len[i] ? (uint32_t)__ldg(ap[i] + at[i]) : MKEY_END;
-                    }
+            // one k-way merge of the key's sorted arrays, duplicates once,
+            // compiled for each member count
+            switch (k) {
+                case 1: n = kway_merge<1>(P, mem, MS, X, lane); break;
+                case 2: n = kway_merge<2>(P, mem, MS, X, lane); break;
+                case 3: n = kway_merge<3>(P, mem, MS, X, lane); break;
+                case 4: n = kway_merge<4>(P, mem, MS, X, lane); break;
+                case 5: n = kway_merge<5>(P, mem, MS, X, lane); break;
+                case 6: n = kway_merge<6>(P, mem, MS, X, lane); break;
+                case 7: n = kway_merge<7>(P, mem, MS, X, lane); break;
+                default: n = kway_merge<8>(P, mem, MS, X, lane); break;
             }
         }
     }
