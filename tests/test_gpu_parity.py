@@ -374,3 +374,32 @@ def test_plan_launch_and_collect(rb, orc, workloads_mod):
             assert int(j[i]) == O[a[i]].op_card(0, O[b[i]])
     with pytest.raises(rb.RoaringError):
         pm.collect()                   # nothing launched
+
+
+def test_readme_example(rb, orc):
+    """The usage example of the README, checked against numpy."""
+    va = np.arange(0, 1 << 20, 3, dtype=np.uint32)
+    vb = np.arange(0, 1 << 20, 5, dtype=np.uint32)
+    a = rb.Bitmap.from_sorted(va)
+    b = rb.Bitmap.from_sorted(vb)
+    c = a & b
+    inter = np.intersect1d(va, vb)
+    assert c.card == len(inter) and np.array_equal(c.to_numpy(), inter)
+    assert a.op_card(rb.OR, b) == len(np.union1d(va, vb))
+    j, i, u = a.jaccard(b)
+    assert (i, u) == (len(inter), len(np.union1d(va, vb)))
+    assert a.cosine(b) == orc.Bitmap.from_sorted(va).cosine(orc.Bitmap.from_sorted(vb))
+    assert (15 in c) and (16 not in c)
+    assert np.array_equal((a ^ b).to_numpy(), np.setxor1d(va, vb))
+    assert np.array_equal((a - b).to_numpy(), np.setdiff1d(va, vb))
+    plan = rb.Plan([a, b], ops=[rb.AND, rb.OR], a=[0, 0], b=[1, 1])
+    outs, counts = plan.run()
+    assert list(counts) == [len(inter), len(np.union1d(va, vb))]
+    union, card = rb.multi_op(rb.OR, [a, b, c])
+    assert card == len(np.union1d(va, vb)) and np.array_equal(union.to_numpy(), np.union1d(va, vb))
+    acc = rb.Accumulator(rb.OR)
+    acc.add(a).add(b)
+    assert acc.result()[1] == len(np.union1d(va, vb))
+    acc.close()
+    img = c.serialize()
+    assert rb.Bitmap.deserialize(img).card == c.card
