@@ -495,6 +495,63 @@ __device__ __forceinline__ void flush_sums(PairStats *stats, uint32_t p, unsigne
     __syncwarp();
 }
 
+// driver mode (skewed AND/ANDNOT/count queries), out of the hot path: slot's
+// key from the driving list, found in the other by binary search; returns
+// kind | key << 16, ia, ib
+__device__ __noinline__ uint4 resolve_driven(const BmView &A, const BmView &B, uint32_t slot, bool and_like,
+                                             bool count_only) {
+    uint32_t kind, key, ia = 0, ib = 0;
+    if (and_like) {
+        const bool drvA = A.n <= B.n;
+        const uint16_t *dk = drvA ? A.keys : B.keys;
+        const uint16_t *ok = drvA ? B.keys : A.keys;
+        const uint32_t on = drvA ? B.n : A.n;
+        key = __ldg(dk + slot);
+        const uint32_t j = lower_bound16(ok, on, key);
+        if (j < on && __ldg(ok + j) == key) {
+            kind = K_PAIR;
+            ia = drvA ? slot : j;
+            ib = drvA ? j : slot;
+        } else {
+            kind = count_only ? K_NONE : K_EMPTY;
+        }
+    } else {   // ANDNOT, driven by a
+        key = __ldg(A.keys + slot);
+        const uint32_t j = lower_bound16(B.keys, B.n, key);
+        ia = slot;
+        if (j < B.n && __ldg(B.keys + j) == key) {
+            kind = K_PAIR;
+            ib = j;
+        } else {
+            kind = K_COPY_A;
+        }
+    }
+    return make_uint4(kind | (key << 16), ia, ib, 0u);
+}
+
+// append the tile's container pairs for the heavy kernel (lanes in lm)
+__device__ __noinline__ void queue_deferred(ExecState *es, uint32_t lm, bool mine, uint64_t da, uint64_t db, uint32_t p,
+                                            uint32_t pos, uint32_t kind_key, uint32_t lane) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&es->defer_n, (unsigned long long)__popc(lm));
+    base = __shfl_sync(FULL, base, 0);
+    if (mine) {
+        const unsigned long long at = base + __popc(lm & lanemask_lt(lane));
+        if (at < es->defer_cap) {
+            Deferred d;
+            d.da = da;
+            d.db = db;
+            d.p = p;
+            d.pos = pos;
+            d.kind_key = kind_key;
+            d.pad = 0;
+            es->defer[at] = d;
+        } else {
+            atomicOr(&es->status, 2u);
+        }
+    }
+}
+
 // Key merge of one tile: each lane resolves its slot into a container pair,
 // an empty result, a copy or nothing.  Empty results and copies of array and
 // run containers are finished at once, pairs with a bitset or many values go
@@ -585,29 +642,12 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
     } else {
         const uint32_t slot = local * 32u + lane;
         if (slot < pd.n_slots) {
-            if (count_only || op == OP_AND) {
-                const bool drvA = A.n <= B.n;
-                const uint16_t *dk = drvA ? A.keys : B.keys;
-                const uint16_t *ok = drvA ? B.keys : A.keys;
-                const uint32_t on = drvA ? B.n : A.n;
-                key = __ldg(dk + slot);
-                const uint32_t j = lower_bound16(ok, on, key);
-                pos = slot;
-                if (j < on && __ldg(ok + j) == key) {
-                    kind = K_PAIR;
-                    ia = drvA ? slot : j;
-                    ib = drvA ? j : slot;
-                } else {
-                    kind = count_only ? K_NONE : K_EMPTY;
-                }
-            } else {   // ANDNOT, driven by a
-                key = __ldg(A.keys + slot);
-                const uint32_t j = lower_bound16(B.keys, B.n, key);
-                pos = slot;
-                ia = slot;
-                if (j < B.n && __ldg(B.keys + j) == key) { kind = K_PAIR; ib = j; }
-                else kind = K_COPY_A;
-            }
+            const uint4 rs = resolve_driven(A, B, slot, count_only || op == OP_AND, count_only);
+            kind = rs.x & 0xFFFFu;
+            key = rs.x >> 16;
+            pos = slot;
+            ia = rs.y;
+            ib = rs.z;
         }
     }
     const uint64_t da = (kind == K_PAIR || kind == K_COPY_A) ? __ldg(A.descs + ia) : 0ull;
@@ -634,26 +674,7 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
         mode = d_type(dx) == T_BITSET ? M_DEFER : M_COPY;
     }
     const uint32_t lm = __ballot_sync(FULL, mode == M_DEFER);
-    if (lm) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&es->defer_n, (unsigned long long)__popc(lm));
-        base = __shfl_sync(FULL, base, 0);
-        if (mode == M_DEFER) {
-            const unsigned long long at = base + __popc(lm & lanemask_lt(lane));
-            if (at < es->defer_cap) {
-                Deferred d;
-                d.da = da;
-                d.db = db;
-                d.p = p;
-                d.pos = pos;
-                d.kind_key = (kind << 16) | key;
-                d.pad = 0;
-                es->defer[at] = d;
-            } else {
-                atomicOr(&es->status, 2u);
-            }
-        }
-    }
+    if (lm) queue_deferred(es, lm, mode == M_DEFER, da, db, p, pos, (kind << 16) | key, lane);
     if (kind == K_EMPTY) {
         es->descs[pd.pos_base + pos] = DESC_EMPTY;
         es->keys[pd.pos_base + pos] = (uint16_t)key;
@@ -1057,6 +1078,46 @@ __device__ __forceinline__ void process_groups(ExecState *es, uint32_t gq, const
     }
 }
 
+// Warp-sized array merges of the lanes in wq, one at a time; the first words
+// of the next pair are requested before the current one is merged; each
+// served lane gets its pair's descriptor and cardinality
+__device__ __noinline__ void process_warp_merges(ExecState *es, uint32_t wq, const CRef &ca, const CRef &cb,
+                                                 uint32_t tbl, uint64_t off, bool count, uint16_t *stg, uint32_t lane,
+                                                 uint64_t &desc, uint32_t &card) {
+    auto pre = [&](int k) -> WPre {
+        return prefetch_words(reinterpret_cast<const uint16_t *>(__shfl_sync(FULL, (unsigned long long)ca.p, k)),
+                              __shfl_sync(FULL, ca.card, k),
+                              reinterpret_cast<const uint16_t *>(__shfl_sync(FULL, (unsigned long long)cb.p, k)),
+                              __shfl_sync(FULL, cb.card, k), lane);
+    };
+    WPre w_cur = {0u, 0u};
+    if (wq) w_cur = pre(__ffs(wq) - 1);
+    while (wq) {
+        const int src = __ffs(wq) - 1;
+        wq &= wq - 1;
+        WPre w_next = {0u, 0u};
+        if (wq) w_next = pre(__ffs(wq) - 1);
+        const uint32_t tbl_s = __shfl_sync(FULL, tbl, src);
+        const uint64_t off_s = __shfl_sync(FULL, count ? ALLOC_FAIL : off, src);
+        const unsigned long long pa_s = __shfl_sync(FULL, (unsigned long long)ca.p, src);
+        const unsigned long long pb_s = __shfl_sync(FULL, (unsigned long long)cb.p, src);
+        const uint32_t na_s = __shfl_sync(FULL, ca.card, src), nb_s = __shfl_sync(FULL, cb.card, src);
+        uint32_t c = 0;
+        uint64_t dsc = DESC_EMPTY;
+        if (__shfl_sync(FULL, (uint32_t)count, src))
+            c = warp_count_arrays(reinterpret_cast<const uint16_t *>(pa_s), na_s,
+                                  reinterpret_cast<const uint16_t *>(pb_s), nb_s, w_cur, stg, lane);
+        else
+            dsc = warp_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s), na_s,
+                                    reinterpret_cast<const uint16_t *>(pb_s), nb_s, w_cur, stg, lane, off_s, c);
+        w_cur = w_next;
+        if (lane == (uint32_t)src) {
+            desc = dsc;
+            card = c;
+        }
+    }
+}
+
 // Process n <= 32 queued container pairs, one per lane (warp-sized ones by
 // the whole warp in turn), with one allocation for all their outputs.  The
 // queue holds pairs only: copies are done during the key merge.
@@ -1135,41 +1196,9 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     // group-sized array merges, GPER at a time
     const uint32_t gq = __ballot_sync(FULL, mode == M_GRP_ARR);
     if (gq) process_groups(es, gq, ca, cb, tbl, off, count, stg, lane, desc, card);
-    // warp-sized array merges, one at a time; the first words of the next
-    // pair are requested before the current one is merged
-    uint32_t wq = __ballot_sync(FULL, mode == M_WARP_ARR);
-    auto pre = [&](int k) -> WPre {
-        return prefetch_words(reinterpret_cast<const uint16_t *>(__shfl_sync(FULL, (unsigned long long)ca.p, k)),
-                              __shfl_sync(FULL, ca.card, k),
-                              reinterpret_cast<const uint16_t *>(__shfl_sync(FULL, (unsigned long long)cb.p, k)),
-                              __shfl_sync(FULL, cb.card, k), lane);
-    };
-    WPre w_cur = {0u, 0u};
-    if (wq) w_cur = pre(__ffs(wq) - 1);
-    while (wq) {
-        const int src = __ffs(wq) - 1;
-        wq &= wq - 1;
-        WPre w_next = {0u, 0u};
-        if (wq) w_next = pre(__ffs(wq) - 1);
-        const uint32_t tbl_s = __shfl_sync(FULL, tbl, src);
-        const uint64_t off_s = __shfl_sync(FULL, count ? ALLOC_FAIL : off, src);
-        const unsigned long long pa_s = __shfl_sync(FULL, (unsigned long long)ca.p, src);
-        const unsigned long long pb_s = __shfl_sync(FULL, (unsigned long long)cb.p, src);
-        const uint32_t na_s = __shfl_sync(FULL, ca.card, src), nb_s = __shfl_sync(FULL, cb.card, src);
-        uint32_t c = 0;
-        uint64_t dsc = DESC_EMPTY;
-        if (__shfl_sync(FULL, (uint32_t)count, src))
-            c = warp_count_arrays(reinterpret_cast<const uint16_t *>(pa_s), na_s,
-                                  reinterpret_cast<const uint16_t *>(pb_s), nb_s, w_cur, stg, lane);
-        else
-            dsc = warp_merge_arrays(es, tbl_s, reinterpret_cast<const uint16_t *>(pa_s), na_s,
-                                    reinterpret_cast<const uint16_t *>(pb_s), nb_s, w_cur, stg, lane, off_s, c);
-        w_cur = w_next;
-        if (lane == (uint32_t)src) {
-            desc = dsc;
-            card = c;
-        }
-    }
+    // warp-sized array merges, one at a time (pairs of 255..1022 values)
+    const uint32_t wq = __ballot_sync(FULL, mode == M_WARP_ARR);
+    if (wq) process_warp_merges(es, wq, ca, cb, tbl, off, count, stg, lane, desc, card);
     // results, and per-query sums over the lanes of the same query
     if (has && !count) {
         es->descs[pd.pos_base + it.pos] = desc;
