@@ -239,7 +239,7 @@ void rb_plan_free(rb_plan_t *p);
  * the largest array pair (values on both sides) that one lane of the lean
  * kernel merges alone (larger array pairs up to 1024 values are merged by the
  * whole warp; bitsets and larger containers are deferred to the heavy
- * kernel); the lean kernel's CTAs of 128 threads per SM (0 = 7, the most that fit); and how many
+ * kernel); the lean kernel's CTAs of 128 threads per SM (0 = 8, the most that fit); and how many
  * 128-byte lines of each queued container's payload the lean kernel hints
  * into L2 ahead of use (0 = none). */
 typedef struct {

@@ -475,7 +475,7 @@ rb_status rb_set_schedule(const rb_schedule *s) {
     if (s->ctas_per_sm < 1 || s->ctas_per_sm * s->warps_per_cta * 16384u > 228u * 1024u)
         return set_err(RB_EINVAL, "ctas_per_sm out of range for 16 KB of tiles per warp");
     if (s->small_intervals > 2047) return set_err(RB_EINVAL, "small_intervals must be <= 2047");
-    if (s->lean_ctas_per_sm > 7) return set_err(RB_EINVAL, "lean_ctas_per_sm must be <= 7");
+    if (s->lean_ctas_per_sm > 8) return set_err(RB_EINVAL, "lean_ctas_per_sm must be <= 8");
     if (s->prefetch_lines > 64) return set_err(RB_EINVAL, "prefetch_lines must be <= 64");
     std::lock_guard<std::mutex> g(g_sched_mu);
     g_sched = *s;

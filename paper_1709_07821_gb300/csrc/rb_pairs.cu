@@ -41,9 +41,10 @@ namespace {
 constexpr uint32_t F_COUNT = 1, F_MERGE = 2;
 enum : uint32_t { K_NONE = 0, K_EMPTY = 1, K_PAIR = 2, K_COPY_A = 3, K_COPY_B = 4 };
 constexpr int LEAN_THREADS = 128;
-// resident k_lean CTAs per SM: the register bound (72 per thread) that keeps
-// the kernel free of most spills
-constexpr uint32_t LEAN_CTAS_MAX = 7;
+// resident k_lean CTAs per SM: a bound of 64 registers per thread (40 bytes
+// of spills) and 21.7 KB of shared memory per CTA, which leaves about 60 KB
+// of each SM's L1 for the one-lane merges' payload streams
+constexpr uint32_t LEAN_CTAS_MAX = 8;
 constexpr uint32_t KEY_END = 0x10000u;   // past-the-end key sentinel
 // algorithmic bytes of a container's key and metadata (key 2, type 1,
 // cardinality 4, payload offset 8), whatever the layout packs them into,
@@ -1129,6 +1130,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     it.da = it.db = 0;
     it.p = it.pos = it.info = it.pad = 0;
     if (has) it = q[lane];
+    __syncwarp();   // the items are read before the staging area (queue slots 32..63) is written
     const uint32_t mode = has ? (it.info >> 20) & 7u : M_NONE;
     const uint32_t key = it.info & 0xFFFFu;
     const PairDev pd = P.pairs[it.p];
@@ -1219,10 +1221,16 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
 
 __global__ void __launch_bounds__(LEAN_THREADS, LEAN_CTAS_MAX) k_lean(PairParams P) {
     __shared__ uint32_t s_win[LEAN_THREADS / 32][66];
-    __shared__ Item s_q[LEAN_THREADS / 32][QCAP];
-    __shared__ __align__(16) uint16_t s_stg[LEAN_THREADS / 32][2 * WARP_MERGE_MAX];
+    // per warp: the item queue, whose upper half (slots 32..63) is also the
+    // start of the merge staging area: the upper slots are filled only while
+    // a tile is resolved, and process_items reads its items into registers
+    // before it stages anything, while at most 31 items (slots 0..30) wait
+    static_assert(QCAP == 64 && sizeof(Item) == 32, "queue slot 32 starts the staging area");
+    __shared__ __align__(16) uint8_t s_wq[LEAN_THREADS / 32][(QCAP / 2) * sizeof(Item) + 4 * WARP_MERGE_MAX];
     __shared__ unsigned long long s_alloc[LEAN_THREADS / 32][4];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Item *q = reinterpret_cast<Item *>(s_wq[warp]);
+    uint16_t *stg = reinterpret_cast<uint16_t *>(s_wq[warp] + (QCAP / 2) * sizeof(Item));
     if (lane == 0) s_alloc[warp][0] = s_alloc[warp][1] = s_alloc[warp][2] = s_alloc[warp][3] = 0;
     __syncwarp();
     uint32_t qn = 0;
@@ -1243,12 +1251,12 @@ __global__ void __launch_bounds__(LEAN_THREADS, LEAN_CTAS_MAX) k_lean(PairParams
                 }
                 t_end = min(t + P.chunk, P.n_tiles);
             }
-            resolve_tile(P, t, cur, s_win[warp], s_q[warp], qn, s_alloc[warp], bytes_acc, lane);
+            resolve_tile(P, t, cur, s_win[warp], q, qn, s_alloc[warp], bytes_acc, lane);
             t++;
         }
         if (qn == 0) break;
         const uint32_t take = qn < 32 ? qn : 32;
-        process_items(P, s_q[warp] + (qn - take), take, s_stg[warp], s_alloc[warp], bytes_acc, lane);
+        process_items(P, q + (qn - take), take, stg, s_alloc[warp], bytes_acc, lane);
         qn -= take;
         __syncwarp();
     }
