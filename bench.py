@@ -33,6 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_PAIRS = 65536
+# the workload both arms name in their JSON line
+WORKLOAD = ("batched: 4096-bitmap pool over [0,2^32), c log-uniform 10..1e7, 40/30/30 sparse/dense/runs; "
+            "65,536 pairs AND/OR/ANDNOT/XOR 40/30/15/15 materialised + Jaccard count batch")
 
 
 def log(*a):
@@ -260,9 +263,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": "batched Roaring AND/OR Gints/s", "value": value, "unit": "Gints/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16/u64 integer", "data": "synthetic (seeded)",
-            "config": {"workload": "batched: 4096-bitmap pool over [0,2^32), c log-uniform 10..1e7, "
-                                   "40/30/30 sparse/dense/runs; 65,536 pairs AND/OR/ANDNOT/XOR 40/30/15/15 "
-                                   "materialised + Jaccard", "global_batch": N_PAIRS},
+            "config": {"workload": WORKLOAD, "global_batch": N_PAIRS},
             "cpu_baseline": dict(res, value=value),
             "e2e": {"value": value, "unit": "Gints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -410,9 +411,7 @@ def run_ours(args):
     line = {"metric": "batched Roaring AND/OR Gints/s", "value": value, "unit": "Gints/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u16/u64 integer", "data": "synthetic (seeded)",
-            "config": {"workload": "batched: 4096-bitmap pool over [0,2^32), c log-uniform 10..1e7, 40/30/30 "
-                                   "sparse/dense/runs; 65,536 pairs AND/OR/ANDNOT/XOR 40/30/15/15 materialised "
-                                   "+ Jaccard count batch", "global_batch": n_pairs * ws,
+            "config": {"workload": WORKLOAD, "global_batch": n_pairs * ws,
                        "pool_bytes": pool_bytes, "units_per_step": units_total,
                        "l2": "inputs larger than L2 (pool and outputs are GBs), no flush",
                        "parallelism": f"replicas x{ws}", "schedule": rb.get_schedule()},
