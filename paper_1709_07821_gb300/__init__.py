@@ -180,6 +180,24 @@ def version() -> str:
     return lib().rb_version().decode()
 
 
+U32_MAX = 0xFFFFFFFF
+
+
+def _u32(values, what: str) -> np.ndarray:
+    """values as a contiguous uint32 array; raises rather than wrap a value
+    outside [0, 2^32) or truncate a non-integer one."""
+    v = np.asarray(values)
+    if v.size == 0:
+        return np.zeros(0, np.uint32)
+    if v.dtype.kind not in "iub":
+        raise TypeError(f"{what} must be integers, got {v.dtype}")
+    if v.dtype.kind == "i" or v.dtype.itemsize > 4:
+        lo, hi = int(v.min()), int(v.max())
+        if lo < 0 or hi > U32_MAX:
+            raise ValueError(f"{what} must lie in [0, 2^32), got values in [{lo}, {hi}]")
+    return np.ascontiguousarray(v, dtype=np.uint32)
+
+
 class Bitmap:
     """Handle on a device-resident canonical Roaring bitmap."""
 
@@ -202,7 +220,7 @@ class Bitmap:
             _check(L.rb_from_sorted_u32(ctypes.c_void_p(t.data_ptr()), t.numel(), 1, _stream(stream),
                                         ctypes.byref(h)))
         else:
-            v = np.ascontiguousarray(values, dtype=np.uint32)
+            v = _u32(values, "values")
             _check(L.rb_from_sorted_u32(v.ctypes.data if v.size else None, v.size, 0, _stream(stream),
                                         ctypes.byref(h)))
         return cls(h.value)
@@ -300,10 +318,21 @@ class Bitmap:
             out = torch.empty(v.numel(), dtype=torch.uint8, device=v.device)
             _check(lib().rb_contains_many(self._h, v.data_ptr(), v.numel(), 1, out.data_ptr(), _stream(stream)))
             return out
-        v = np.ascontiguousarray(values, dtype=np.uint32)
-        out = np.empty(v.size, dtype=np.uint8)
-        if v.size:
-            _check(lib().rb_contains_many(self._h, v.ctypes.data, v.size, 0, out.ctypes.data, _stream(stream)))
+        v = np.asarray(values)
+        if v.size and v.dtype.kind not in "iub":
+            raise TypeError(f"values must be integers, got {v.dtype}")
+        v = v.reshape(-1)
+        # a value outside [0, 2^32) is not a member
+        if v.dtype.kind == "i" or v.dtype.itemsize > 4:
+            inside = (v >= 0) & (v <= U32_MAX)
+        else:
+            inside = np.ones(v.size, bool)
+        out = np.zeros(v.size, dtype=np.uint8)
+        w = np.ascontiguousarray(v[inside], dtype=np.uint32)
+        if w.size:
+            got = np.empty(w.size, dtype=np.uint8)
+            _check(lib().rb_contains_many(self._h, w.ctypes.data, w.size, 0, got.ctypes.data, _stream(stream)))
+            out[inside] = got
         return out
 
     def serialize(self, stream=None) -> bytes:
@@ -322,6 +351,9 @@ class Bitmap:
         return cls(h.value)
 
     def __contains__(self, value):
+        value = int(value)
+        if not 0 <= value <= U32_MAX:
+            return False
         r = ctypes.c_int()
         _check(lib().rb_contains(self._h, int(value), ctypes.byref(r)))
         return bool(r.value)
@@ -361,10 +393,10 @@ def _queries(ops, a, b, flags=None):
     q = (Query * max(1, n))()
     arr = np.frombuffer(q, dtype=np.uint32, count=4 * n).reshape(n, 4) if n else None
     if n:
-        arr[:, 0] = ops
-        arr[:, 1] = a
-        arr[:, 2] = b
-        arr[:, 3] = 0 if flags is None else flags
+        arr[:, 0] = _u32(ops, "ops")
+        arr[:, 1] = _u32(a, "pool indexes")
+        arr[:, 2] = _u32(b, "pool indexes")
+        arr[:, 3] = 0 if flags is None else _u32(flags, "flags")
     return q
 
 
@@ -390,8 +422,10 @@ def free_handles(outs, n: int):
 
 
 def batch_jaccard(pool, a, b, stream=None):
-    a = np.ascontiguousarray(a, np.uint32)
-    b = np.ascontiguousarray(b, np.uint32)
+    a = _u32(a, "pool indexes")
+    b = _u32(b, "pool indexes")
+    if len(a) != len(b):
+        raise ValueError("a and b must have the same length")
     n = len(a)
     j = np.zeros(n, np.float64)
     i = np.zeros(n, np.uint64)

@@ -118,3 +118,33 @@ def test_accumulator_argument_checks_without_gpu(librb):
     assert librb.rb_accum_create(1, 65537, None, ctypes.byref(out)) == 1     # more tiles than keys
     assert librb.rb_accum_create(1, 10, None, None) == 1
     assert out.value is None
+
+
+def test_binding_rejects_values_outside_u32_without_gpu(librb):
+    """The binding narrows user values to uint32 only when they fit: out-of-range
+    or non-integer values raise before any device work, and a value outside
+    [0, 2^32) is never reported as a member (it would otherwise wrap)."""
+    import numpy as np
+    import paper_1709_07821_gb300 as rb
+    for bad in (np.array([-1, 5]), np.array([1, 2 ** 32], dtype=np.int64), np.array([3, 2 ** 40], dtype=np.uint64)):
+        with pytest.raises(ValueError):
+            rb.Bitmap.from_sorted(bad)
+    with pytest.raises(TypeError):
+        rb.Bitmap.from_sorted(np.array([1.0, 2.5]))
+    with pytest.raises(ValueError):
+        rb._queries([0], [2 ** 32 + 3], [1])
+    with pytest.raises(ValueError):
+        rb._queries([0], [1], [-2])
+    with pytest.raises(ValueError):
+        rb.batch_jaccard([], [1], [1, 2])
+    unbound = rb.Bitmap(None)            # no device bitmap: these answers need none
+    assert (2 ** 32 + 5) not in unbound and -1 not in unbound
+    got = unbound.contains(np.array([-1, 2 ** 32, 2 ** 40], dtype=np.int64))
+    assert got.dtype == np.uint8 and got.tolist() == [0, 0, 0]
+    with pytest.raises(TypeError):
+        unbound.contains(np.array([0.5]))
+    # in-range inputs pass through unchanged, without a copy for uint32
+    v = np.array([0, 7, 2 ** 32 - 1], dtype=np.uint32)
+    assert rb._u32(v, "v") is v
+    assert rb._u32(np.array([0, 2 ** 32 - 1], dtype=np.int64), "v").tolist() == [0, 2 ** 32 - 1]
+    assert rb._u32([], "v").dtype == np.uint32
