@@ -323,7 +323,9 @@ rb_status rb_server_submit(rb_server_t *s, const rb_request *r, uint64_t *ticket
 /* Wait (at most timeout_ms) for a ticket.  *out (may be NULL) receives the
  * result bitmap of a materialising request (caller frees it); *card its
  * cardinality; *latency_s the time from submit to completion on the device.
- * RB_ETIMEOUT if it is not done in time (the ticket stays valid). */
+ * RB_ETIMEOUT if it is not done in time (the ticket stays valid); RB_EINVAL
+ * for an unknown ticket, or one that rb_server_poll collected meanwhile.
+ * Safe to call from several threads while others submit and poll. */
 rb_status rb_server_wait(rb_server_t *s, uint64_t ticket, int timeout_ms, rb_t **out,
                          uint64_t *card, double *latency_s);
 /* Queue n requests at once (a frontend draining its input in bursts): the

@@ -369,13 +369,19 @@ rb_status rb_server_wait(rb_server_t *S, uint64_t ticket, int timeout_ms, rb_t *
     if (out) *out = nullptr;
     if (!S) return set_err(RB_EINVAL, "rb_server_wait: NULL server");
     std::unique_lock<std::mutex> lk(S->mu);
+    const auto deadline = clk::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    // the ticket is looked up again after every wait: while the lock is
+    // released a submission may rehash the map and a poll may collect the
+    // ticket
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return set_err(RB_EINVAL, "unknown ticket %llu", (unsigned long long)ticket);
-    const auto deadline = clk::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
     while (it->second.state != 2) {
-        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && it->second.state != 2)
-            return set_err(RB_ETIMEOUT, "ticket %llu not done within %d ms", (unsigned long long)ticket, timeout_ms);
+        const bool timed_out = S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout;
         it = S->reqs.find(ticket);
+        if (it == S->reqs.end())
+            return set_err(RB_EINVAL, "ticket %llu was collected by another call", (unsigned long long)ticket);
+        if (timed_out && it->second.state != 2)
+            return set_err(RB_ETIMEOUT, "ticket %llu not done within %d ms", (unsigned long long)ticket, timeout_ms);
     }
     Req r = it->second;
     S->reqs.erase(it);

@@ -182,3 +182,51 @@ def test_results_outlive_the_server(env):
         for k in ("keys", "types", "cards", "offs", "payload"):
             assert np.array_equal(lay[k], ref[k]), (q, k)
         bm.free()
+
+
+def test_wait_beside_concurrent_submits_and_polls(env):
+    """rb_server_wait looks its ticket up again after every wake: waiter
+    threads block while another thread submits hundreds of requests (the
+    ticket map grows through several rehashes), and a ticket that a poll
+    collected is reported to a later wait as unknown (RB_EINVAL)."""
+    rb, orc, W, pool, G, O = env
+    ops, ks, co, mem = W.multi_queries(53, 64, pool.n)
+    count = np.ones(len(ops), np.uint8)
+    srv = rb.Server(G, mem_budget=8 << 30, max_inflight_batches=4, max_batch=8)
+    try:
+        tickets = srv.submit_many(ops, ks, count, mem)
+        got, errs = {}, []
+
+        def waiter(lo, hi):
+            try:
+                for q in range(lo, hi):
+                    _, card, _ = srv.wait(int(tickets[q]), timeout_ms=120000, want_bitmap=False)
+                    got[q] = card
+            except Exception as e:   # reported below, on the main thread
+                errs.append(e)
+
+        ws = [threading.Thread(target=waiter, args=(16 * i, 16 * (i + 1))) for i in range(4)]
+        for w in ws:
+            w.start()
+        more = sum(len(srv.submit_many(ops, ks, count, mem)) for _ in range(8))
+        for w in ws:
+            w.join()
+        assert not errs, errs
+        for q in range(len(ops)):
+            assert got[q] == orc.Bitmap.multi(int(ops[q]), [O[m] for m in mem[q, :ks[q]]]).card, q
+        seen = 0
+        while seen < more:
+            t, st, _, _, _ = srv.poll(cap=1024, timeout_ms=120000)
+            assert len(t) > 0 and np.all(st == 0)
+            seen += len(t)
+        t1 = srv.submit(int(ops[0]), mem[0, :ks[0]].tolist(), True)
+        collected = []
+        while t1 not in collected:
+            t, _, _, _, _ = srv.poll(cap=8, timeout_ms=120000)
+            assert len(t) > 0
+            collected.extend(int(x) for x in t)
+        with pytest.raises(rb.RoaringError) as ei:
+            srv.wait(t1, timeout_ms=1000)
+        assert ei.value.status == rb.EINVAL
+    finally:
+        srv.close()
