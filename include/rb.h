@@ -211,8 +211,9 @@ rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream)
  * `stream` ordered after it) and returns at once; rb_plan_collect waits for
  * it, reruns it with exact sizes if its output space ran out, and fills outs
  * and counts as rb_plan_run does.  One run per plan may be outstanding
- * (RB_EINVAL otherwise, and for a collect without a launch); several plans
- * launched on one stream run one after another on the device. */
+ * (RB_EINVAL otherwise, and for a collect without a launch); rb_plan_run and
+ * rb_autotune on a plan with an outstanding run return RB_EINVAL; several
+ * plans launched on one stream run one after another on the device. */
 rb_status rb_plan_launch(rb_plan_t *p, void *stream);
 rb_status rb_plan_collect(rb_plan_t *p, rb_t **outs, uint64_t *counts);
 /* Measurements of the last run, from CUDA events on the stream the kernels

@@ -2107,6 +2107,8 @@ rb_status rb_plan_create(const rb_t *const *pool, uint32_t pool_n, const rb_quer
 
 rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream) {
     if (!p) return set_err(RB_EINVAL, "rb_plan_run: NULL plan");
+    // a launched run owns the plan's execution state until it is collected
+    if (p->pending) return set_err(RB_EINVAL, "rb_plan_run: a launched run has not been collected");
     if (outs)
         for (uint64_t i = 0; i < p->q.size(); i++) outs[i] = nullptr;
     if (p->any_mat && !outs) return set_err(RB_EINVAL, "rb_plan_run: outs is NULL but the plan materialises");
@@ -2158,12 +2160,13 @@ void rb_plan_free(rb_plan_t *p) { plan_destroy(p); }
 
 rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *best, double *best_ms) {
     if (!p) return set_err(RB_EINVAL, "rb_autotune: NULL plan");
+    if (p->pending) return set_err(RB_EINVAL, "rb_autotune: a launched run has not been collected");
     if (reps == 0) reps = 1;
     cudaStream_t s = (cudaStream_t)stream;
     const rb_schedule saved = current_schedule();
     static const uint32_t heavy[][2] = {{2, 6}, {4, 3}, {8, 1}};
     static const uint32_t smalls[] = {64, 256, 512};
-    static const uint32_t leans[] = {4, 7};
+    static const uint32_t leans[] = {4, LEAN_CTAS_MAX};
     rb_schedule win = saved;
     double win_ms = 1e30;
     std::vector<rb_t *> outs(p->q.size(), nullptr);

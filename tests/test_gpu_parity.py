@@ -365,6 +365,9 @@ def test_plan_launch_and_collect(rb, orc, workloads_mod):
         pj.launch()
         with pytest.raises(rb.RoaringError):
             pm.launch()                # one outstanding run per plan
+        with pytest.raises(rb.RoaringError) as ei:
+            pm.run()                   # the launched run owns the plan until collected
+        assert ei.value.status == rb.EINVAL
         got, c = pm.collect()
         _, j = pj.collect(want_bitmaps=False)
         assert np.array_equal(c, cref) and np.array_equal(j, jref)
