@@ -115,7 +115,10 @@ void arena_unref_n(RbArena *a, int n) {
         else dev_free(a->ptr, a->bytes, a->stream);
         if (a->budget) {
             a->budget->used.fetch_sub((int64_t)a->charge);
-            if (a->budget->notify) a->budget->notify(a->budget->ctx);
+            {
+                std::lock_guard<std::mutex> g(a->budget->mu);
+                if (a->budget->notify) a->budget->notify(a->budget->ctx);
+            }
             budget_unref(a->budget);
         }
         delete a;

@@ -65,11 +65,16 @@ struct BmView {
 
 // ------------------------------------------------------------------ host side
 
+#include <mutex>
+
 // memory budget shared by a serving loop and the result arenas it hands out;
-// it lives until the loop and every arena charged to it are gone
+// it lives until the loop and every arena charged to it are gone.  notify
+// (the loop's wake-up, with the loop as ctx) is called and cleared under mu,
+// so that no call is in progress once the loop has cleared it
 struct RbBudget {
     std::atomic<int64_t> used;
     std::atomic<int> refs;
+    std::mutex mu;
     void (*notify)(void *ctx);
     void *ctx;
 };

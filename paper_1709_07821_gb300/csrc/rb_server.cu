@@ -423,7 +423,11 @@ void rb_server_destroy(rb_server_t *S) {
         if (sl.stage.p) cudaFreeHost(sl.stage.p);
     }
     if (S->d_index) cudaFree(S->d_index);
-    S->budget->notify = nullptr;
+    {
+        // results that outlive the loop stop waking it before it is deleted
+        std::lock_guard<std::mutex> g(S->budget->mu);
+        S->budget->notify = nullptr;
+    }
     budget_unref(S->budget);
     delete S;
 }
