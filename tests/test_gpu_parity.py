@@ -78,7 +78,8 @@ def test_fig1_on_gpu(rb, orc):
 @pytest.mark.parametrize("size", ["small", "large"])
 def test_container_pair_classes(rb, orc, ka, kb, size):
     """Every type pair x op, on one shared key plus unmatched keys on each side."""
-    rng = np.random.default_rng(hash((ka, kb, size)) % 2**32)
+    kinds, sizes = ("array", "bitset", "run"), ("small", "large")
+    rng = np.random.default_rng(3000 + 100 * kinds.index(ka) + 10 * kinds.index(kb) + sizes.index(size))
     a = np.concatenate([chunk(rng, 1, ka, size), chunk(rng, 7, ka, size), chunk(rng, 9, "array", "small")])
     b = np.concatenate([chunk(rng, 3, kb, size), chunk(rng, 7, kb, size), chunk(rng, 12, "run", "small")])
     A, B, OA, OB = build_pair(rb, orc, a, b)
@@ -406,3 +407,30 @@ def test_readme_example(rb, orc):
     acc.close()
     img = c.serialize()
     assert rb.Bitmap.deserialize(img).card == c.card
+
+
+def test_autotune_then_results_match_the_oracle(rb, orc, workloads_mod):
+    """rb_autotune searches schedules on a plan, installs the fastest, and
+    the plan's results under it equal the oracle's (schedules change speed,
+    never results)."""
+    pool = _pool(workloads_mod, "batched", 40, 5.3, seed=61)
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    O = [orc.Bitmap.from_sorted(v) for v in vals]
+    ops, a, b = workloads_mod.pairs(62, 240, pool.n)
+    plan = rb.Plan(G, ops, a, b)
+    saved = rb.get_schedule()
+    try:
+        best, ms = plan.autotune(reps=1)
+        assert ms > 0 and rb.get_schedule() == best
+        assert best["small_intervals"] in (32, 48, 64, 96, 128) and best["lean_ctas_per_sm"] in (6, 7, 8)
+        assert best["prefetch_lines"] in (0, 2, 4, 8)
+        outs, counts = plan.run()
+        for i in range(len(ops)):
+            exp = O[a[i]].op(int(ops[i]), O[b[i]])
+            assert int(counts[i]) == exp.card, i
+            assert_layout_eq(outs[i].layout(), exp.layout(), f"tuned pair {i}")
+    finally:
+        rb.set_schedule(saved["warps_per_cta"], saved["ctas_per_sm"], saved["small_intervals"],
+                        saved["lean_ctas_per_sm"], saved["prefetch_lines"])
+        plan.free()
