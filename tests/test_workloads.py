@@ -47,3 +47,21 @@ def test_pairs(workloads_mod):
     for q in range(50):
         m = mem[q, :k[q]]
         assert len(np.unique(m)) == k[q]
+
+
+def test_slices_of_a_pool_equal_the_whole_pool(workloads_mod):
+    """make_pool_some draws chosen bitmaps of a pool with the values and
+    classes the whole pool gives them (large pools are built a slice at a
+    time)."""
+    W = workloads_mod
+    spec = W.scaled(W.SPECS["serving"], n_bitmaps=40, log10_hi=5.0)
+    whole = W.make_pool(spec)
+    for lo, hi in W.slices(40, 16):
+        part = W.make_pool_some(spec, np.arange(lo, hi))
+        for j, i in enumerate(range(lo, hi)):
+            assert np.array_equal(part.values(j), whole.values(i)) and part.klass(j) == whole.klass(i)
+    pick = W.make_pool_some(spec, [39, 0, 7])
+    assert np.array_equal(pick.values(0), whole.values(39))
+    import pytest
+    with pytest.raises(MemoryError):
+        W.make_pool_some(spec, [40])

@@ -63,6 +63,8 @@ def _load():
         vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
         lib.gen_pool_create.restype = vp
         lib.gen_pool_create.argtypes = [ctypes.POINTER(_Params), ctypes.c_int]
+        lib.gen_pool_create_some.restype = vp
+        lib.gen_pool_create_some.argtypes = [ctypes.POINTER(_Params), vp, u32, ctypes.c_int]
         lib.gen_plain_pair.restype = vp
         lib.gen_plain_pair.argtypes = [u64]
         lib.gen_pool_free.argtypes = [vp]
@@ -172,6 +174,46 @@ def make_pool(spec: PoolSpec, threads: int | None = None) -> Pool:
     if not h:
         raise MemoryError("workload generation failed")
     return Pool(h, lib)
+
+
+def make_pool_some(spec: PoolSpec, idx, threads: int | None = None) -> Pool:
+    """Bitmaps idx of the pool `spec` describes (set j is bitmap idx[j], with
+    the same values make_pool(spec) gives it), so that a large pool can be
+    drawn a slice at a time."""
+    lib = _load()
+    p = _Params(spec.seed, spec.n_bitmaps, spec.universe_log2, spec.log10_lo, spec.log10_hi,
+                spec.pm_sparse, spec.pm_dense, spec.pm_runs, spec.run_k, spec.gap_k,
+                spec.d_lo, spec.d_hi)
+    ix = np.ascontiguousarray(idx, dtype=np.uint32)
+    h = lib.gen_pool_create_some(ctypes.byref(p), ix.ctypes.data if ix.size else None, ix.size,
+                                 int(threads or os.cpu_count() or 1))
+    if not h:
+        raise MemoryError("workload generation failed (or an index is outside the pool)")
+    return Pool(h, lib)
+
+
+def slices(n: int, step: int):
+    """[lo, hi) ranges of step bitmaps covering 0..n."""
+    return [(lo, min(n, lo + step)) for lo in range(0, n, step)]
+
+
+def stream_pool(spec: PoolSpec, consume, step: int = 512, threads: int | None = None):
+    """Hand every bitmap of the pool `spec` describes to consume(i, values),
+    in index order, drawing step bitmaps at a time and releasing each slice
+    before the next (host memory stays at one slice).  Returns (sizes,
+    classes) of the whole pool."""
+    sizes = np.zeros(spec.n_bitmaps, np.uint64)
+    cls = np.zeros(spec.n_bitmaps, np.uint32)
+    for lo, hi in slices(spec.n_bitmaps, step):
+        part = make_pool_some(spec, np.arange(lo, hi), threads)
+        try:
+            for j in range(hi - lo):
+                sizes[lo + j] = part.size(j)
+                cls[lo + j] = part.klass(j)
+                consume(lo + j, part.values(j))
+        finally:
+            part.close()
+    return sizes, cls
 
 
 def plain_pair(seed: int = 1) -> Pool:

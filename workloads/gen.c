@@ -258,6 +258,56 @@ gen_pool *gen_pool_create(const gen_params *p, int threads) {
     return g;
 }
 
+/* bitmaps idx[0..n) of the pool p describes, as a pool of n sets (set j is
+ * bitmap idx[j], with exactly the values gen_pool_create gives it): a large
+ * pool can be drawn a slice at a time */
+typedef struct {
+    const gen_params *p;
+    const uint32_t *idx;
+    uint32_t n, next;
+    gen_pool *pool;
+    pthread_mutex_t mu;
+    int err;
+} some_job_t;
+
+static void *some_worker(void *arg) {
+    some_job_t *j = (some_job_t *)arg;
+    for (;;) {
+        pthread_mutex_lock(&j->mu);
+        uint32_t t = j->next++;
+        pthread_mutex_unlock(&j->mu);
+        if (t >= j->n) break;
+        if (gen_one(j->p, j->idx[t], &j->pool->sets[t], &j->pool->cls[t])) {
+            pthread_mutex_lock(&j->mu); j->err = 1; pthread_mutex_unlock(&j->mu);
+        }
+    }
+    return NULL;
+}
+
+gen_pool *gen_pool_create_some(const gen_params *p, const uint32_t *idx, uint32_t n, int threads) {
+    gen_pool *g = (gen_pool *)calloc(1, sizeof(gen_pool));
+    if (!g) return NULL;
+    g->n = n;
+    g->sets = (vec_t *)calloc(n ? n : 1, sizeof(vec_t));
+    g->cls = (uint8_t *)calloc(n ? n : 1, 1);
+    if (!g->sets || !g->cls) { gen_pool_free(g); return NULL; }
+    for (uint32_t t = 0; t < n; t++)
+        if (idx[t] >= p->n_bitmaps) { gen_pool_free(g); return NULL; }
+    some_job_t j; j.p = p; j.idx = idx; j.n = n; j.next = 0; j.pool = g; j.err = 0;
+    pthread_mutex_init(&j.mu, NULL);
+    if (threads < 1) threads = 1;
+    if (threads > 256) threads = 256;
+    pthread_t th[256];
+    int started = 0;
+    for (int t = 0; t < threads; t++)
+        if (pthread_create(&th[t], NULL, some_worker, &j) == 0) started++;
+    if (started == 0) some_worker(&j);
+    for (int t = 0; t < started; t++) pthread_join(th[t], NULL);
+    pthread_mutex_destroy(&j.mu);
+    if (j.err) { gen_pool_free(g); return NULL; }
+    return g;
+}
+
 uint32_t gen_pool_n(const gen_pool *g) { return g->n; }
 uint64_t gen_pool_size(const gen_pool *g, uint32_t i) { return g->sets[i].n; }
 const uint32_t *gen_pool_values(const gen_pool *g, uint32_t i) { return g->sets[i].v; }
