@@ -148,14 +148,17 @@ void *pinned_scratch(uint64_t bytes) {
     return buf.p;
 }
 
+// SM count of the current device, looked up once per device; concurrent
+// first calls store the same value
 int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+    constexpr int MAX_DEV = 256;
+    static std::atomic<int> cache[MAX_DEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    int n = dev < MAX_DEV ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    if (dev < MAX_DEV) cache[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 

@@ -7,6 +7,8 @@
 // must not block on an allocator).  For them rb_to_u32_noalloc keeps the one
 // piece of scratch the decode needs, the per-container output offsets, in a
 // fixed file-scope device array instead of a fresh allocation.
+#include <cuda.h>   // driver types only: the two driver calls below are looked up at run time
+
 #include <mutex>
 
 #include "rb_internal.h"
@@ -23,7 +25,37 @@ static __device__ __align__(256) unsigned long long g_noalloc_offs[NOALLOC_MAX_C
 
 constexpr int MAX_DEVICES = 256;
 std::mutex g_mu;
-void *g_offs_addr[MAX_DEVICES];   // device address of g_noalloc_offs, per device
+// per device: the device address of g_noalloc_offs and the id of the CUDA
+// context it was looked up in.  cudaDeviceReset destroys that context and the
+// module is loaded again, possibly at another address, in the next one; a
+// call that finds another context id looks the address up again.
+void *g_offs_addr[MAX_DEVICES];
+unsigned long long g_offs_ctx[MAX_DEVICES];
+
+// cuCtxGetCurrent and cuCtxGetId, from the driver through the runtime (the
+// library does not link the driver library itself)
+typedef CUresult (*ctx_current_fn)(CUcontext *);
+typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long *);
+ctx_current_fn g_ctx_current;
+ctx_id_fn g_ctx_id;
+
+// id of the calling thread's current context (0 if none); g_mu held
+bool current_ctx_id(unsigned long long *id) {
+    if (!g_ctx_current || !g_ctx_id) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return false;
+        g_ctx_current = reinterpret_cast<ctx_current_fn>(f1);
+        g_ctx_id = reinterpret_cast<ctx_id_fn>(f2);
+    }
+    CUcontext c = nullptr;
+    if (g_ctx_current(&c) != CUDA_SUCCESS) return false;
+    *id = 0;
+    return !c || g_ctx_id(c, id) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
@@ -47,14 +79,19 @@ extern "C" rb_status rb_to_u32_noalloc(const rb_t *b, uint32_t *dst, uint64_t ca
     if (dev < 0 || dev >= MAX_DEVICES) return set_err(RB_ERANGE, "rb_to_u32_noalloc: device %d out of range", dev);
     void *offs = nullptr;
     {
-        // set-up, once per device, with that device current: in host code the
-        // array's name is only a stand-in, so kernels get its device address
+        // set-up, once per device (and again after a cudaDeviceReset), with
+        // that device current: in host code the array's name is only a
+        // stand-in, so kernels get its device address
         std::lock_guard<std::mutex> g(g_mu);
-        if (!g_offs_addr[dev]) {
+        unsigned long long ctx = 0;
+        if (!current_ctx_id(&ctx)) return set_err(RB_ECUDA, "rb_to_u32_noalloc: no current CUDA context id");
+        if (!g_offs_addr[dev] || !ctx || g_offs_ctx[dev] != ctx) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_offs);
             if (e != cudaSuccess) return cuda_err(e, "rb_to_u32_noalloc: cudaGetSymbolAddress");
+            if (!ctx && !current_ctx_id(&ctx)) return set_err(RB_ECUDA, "rb_to_u32_noalloc: no current CUDA context id");
             g_offs_addr[dev] = p;
+            g_offs_ctx[dev] = ctx;
         }
         offs = g_offs_addr[dev];
     }

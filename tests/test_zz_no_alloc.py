@@ -90,3 +90,20 @@ def test_noalloc_limits(rb):
     small = rb.Bitmap.from_sorted(np.arange(100, dtype=np.uint32))
     st, n, _ = decode_noalloc(rb, small, 50, stream)
     assert st == rb.ERANGE and n == 100
+
+
+def test_noalloc_at_the_container_limit(rb):
+    """16,384 containers (the documented maximum, every entry of the fixed
+    array in use) decode exactly as rb_to_u32 does; 16,385 are refused."""
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    for n_cont, want in ((16384, rb.OK), (16385, rb.ERANGE)):
+        v = (np.arange(n_cont, dtype=np.uint32) << np.uint32(16)) | (np.arange(n_cont, dtype=np.uint32) % 65536)
+        bm = rb.Bitmap.from_sorted(v)
+        assert bm.n_containers == n_cont
+        st, n, out = decode_noalloc(rb, bm, bm.card, stream)
+        assert st == want and n == n_cont, rb.lib().rb_last_error()
+        if want == rb.OK:
+            torch.cuda.synchronize()
+            got = out[:n].cpu().numpy().view(np.uint32)
+            assert np.array_equal(got, bm.to_numpy()) and np.array_equal(got, v)
