@@ -216,10 +216,11 @@ class OracleSample:
         A.jaccard(B)
         return int(self.sizes[self.a[i]]) + int(self.sizes[self.b[i]])
 
-    def time(self, budget_s):
+    def time(self, budget_s, threads=None):
+        threads = threads or self.threads
         done_vals, done_pairs = 0, 0
         t0 = time.perf_counter()
-        with cf.ThreadPoolExecutor(self.threads) as ex:
+        with cf.ThreadPoolExecutor(threads) as ex:
             futs = [ex.submit(self._one, i) for i in self.sample]
             for f in futs:
                 done_vals += f.result()
@@ -229,9 +230,9 @@ class OracleSample:
                         g.cancel()
                     break
         dt = time.perf_counter() - t0
-        return {"value": done_vals / dt / 1e9, "unit": "Gints/s", "cores": self.threads, "kind": "oracle",
+        return {"value": done_vals / dt / 1e9, "unit": "Gints/s", "cores": threads, "kind": "oracle",
                 "sample": f"first {done_pairs} of the {self.n_total} pairs (materialised op + Jaccard each), "
-                          f"{done_vals:,} input values, {dt:.1f}s on {self.threads} host threads"}
+                          f"{done_vals:,} input values, {dt:.1f}s on {threads} host threads"}
 
     def close(self):
         for x in self.built.values():
@@ -239,11 +240,55 @@ class OracleSample:
 
 
 def cpu_oracle_leg(pool, ops, a, b, budget_s=15.0):
+    """The oracle on every host core (the reported baseline) and on one core
+    (the paper's own figures are single-threaded), same pairs."""
     s = OracleSample(pool, ops, a, b)
     try:
-        return s.time(budget_s)
+        res = s.time(budget_s)
+        one = s.time(max(3.0, budget_s / 3), threads=1)
+        res["one_core"] = {"value": one["value"], "unit": one["unit"], "cores": 1, "sample": one["sample"]}
+        res["cpu_model"] = cpu_model()
+        return res
     finally:
         s.close()
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
+def time_tasks(tasks, threads, budget_s):
+    """Run tasks (callables returning input values processed) in order on
+    `threads` host threads until all are done or budget_s has passed;
+    returns (values per second, tasks done, seconds)."""
+    done_vals, done = 0, 0
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        futs = [ex.submit(t) for t in tasks]
+        for f in futs:
+            done_vals += f.result()
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                for g in futs:
+                    g.cancel()
+                break
+    dt = time.perf_counter() - t0
+    return done_vals / dt, done, dt
 
 
 def run_reference(args):
@@ -301,16 +346,14 @@ def run_ours(args):
     if args.serving_only:
         # the serving leg alone (profiling the multi-way kernels)
         rates = tuple(float(x) for x in args.serving_rates.split(","))
-        print(json.dumps({"serving": serving_leg(rb, G, sizes, rates=rates, max_queries=args.serving_queries)}))
+        print(json.dumps({"serving": serving_on_index(rb, args, rates=rates, max_queries=args.serving_queries)}))
         return 0
 
     plan_m = rb.Plan(G, ops, a, b)
     jflags = np.full(n_pairs, rb.Q_COUNT_ONLY, np.uint32)
     plan_j = rb.Plan(G, np.zeros(n_pairs, np.uint32), a, b, jflags)
 
-    if args.autotune:
-        best, ms = plan_m.autotune(reps=1)
-        log(f"autotune: {best} ({ms:.2f} ms)")
+    sched_info = tuned_schedule(rb, plan_m, args)
 
     stream = torch.cuda.current_stream()
 
@@ -405,7 +448,8 @@ def run_ours(args):
 
     # per-pair baseline on the same GPU: rb_apply one pair at a time
     per = per_pair_leg(rb, G, ops, a, b, sizes, n=args.per_pair_sample)
-    serving = None if args.no_serving else serving_leg(rb, G, sizes)
+    cfg_legs = None if args.no_configs else config_legs(rb, args)
+    serving = None if args.no_serving else serving_on_index(rb, args)
     cpu = cpu_oracle_leg(pool, ops, a, b, budget_s=args.cpu_budget) if not args.no_cpu else None
 
     line = {"metric": "batched Roaring AND/OR Gints/s", "value": value, "unit": "Gints/s", "n_gpus": ws,
@@ -414,13 +458,14 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "global_batch": n_pairs * ws,
                        "pool_bytes": pool_bytes, "units_per_step": units_total,
                        "l2": "inputs larger than L2 (pool and outputs are GBs), no flush",
-                       "parallelism": f"replicas x{ws}", "schedule": rb.get_schedule()},
+                       "parallelism": f"replicas x{ws}", "schedule": rb.get_schedule(),
+                       "schedule_source": sched_info},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             # per step: k_lean + k_heavy + k_compact (materialising batch), k_lean + k_heavy (Jaccard batch)
             "gpu_launches": 5 * args.steps,
             "clocks": clk,
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
-            "per_pair": per, "bitset_and_or": bitset_legs, "serving": serving}
+            "per_pair": per, "bitset_and_or": bitset_legs, "configs": cfg_legs, "serving": serving}
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -481,6 +526,233 @@ def bitset_subset_legs(rb, G, pool, sizes, n_pairs=16384, reps=5):
     return out
 
 
+def tuned_schedule(rb, plan, args):
+    """The launch schedule for the benchmark: from the schedule cache (JSON
+    keyed by GPU name and workload) when it has an entry, else by running
+    the library's autotuner (rb_autotune) on the benchmark's own
+    materialising plan, untimed, and storing the result."""
+    import torch
+    if args.no_autotune:
+        return {"source": "library default (--no-autotune)"}
+    key = f"{torch.cuda.get_device_name()}|{WORKLOAD}|pairs={plan.n}|pool={args.pool or 4096}|hi={args.log10_hi or 7}"
+    cache = {}
+    path = args.schedule_cache
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except Exception:
+        cache = {}
+    if key in cache and not args.retune:
+        e = cache[key]
+        sc = e["schedule"]
+        rb.set_schedule(sc["warps_per_cta"], sc["ctas_per_sm"], sc["small_intervals"], sc["lean_ctas_per_sm"],
+                        sc["prefetch_lines"])
+        return {"source": f"schedule cache {path}", "tuned_ms": e.get("ms"), "tuned_at": e.get("at")}
+    t0 = time.perf_counter()
+    best, ms = plan.autotune(reps=1)
+    dt = time.perf_counter() - t0
+    cache[key] = {"schedule": best, "ms": ms, "at": time.strftime("%Y-%m-%dT%H:%M:%S"), "search_s": dt}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path + ".tmp", "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(path + ".tmp", path)
+    except Exception as ex:
+        log(f"schedule cache not written: {ex}")
+    log(f"autotune: {best} ({ms:.2f} ms, search {dt:.1f}s)")
+    return {"source": "rb_autotune on this plan (coordinate descent, untimed)", "tuned_ms": ms, "search_s": dt,
+            "cache": path}
+
+
+def plan_leg(rb, plan, units, steps=10, warmup=3):
+    """Device time per run of a plan (CUDA events on the current stream
+    around a graph replay and its collection), Gints/s over `units` input
+    values, and the dominant kernel's algorithmic GB/s against the HBM peak."""
+    import torch
+    stream = torch.cuda.current_stream()
+    peak, _ = measured_peaks()
+    for _ in range(warmup):
+        outs, _ = plan.run(raw=True)
+        plan.free_raw(outs)
+    ms, st = [], []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs, _ = plan.run(raw=True)
+        e1.record(stream)
+        plan.free_raw(outs)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        st.append(plan.stats())
+    t = statistics.median(ms)
+    lm = statistics.mean(x["lean_ms"] for x in st)
+    hm = statistics.mean(x["heavy_ms"] for x in st)
+    lb = statistics.mean(x["lean_bytes"] for x in st)
+    hb = statistics.mean(x["heavy_bytes"] for x in st)
+    kern, kms, kb = ("k_lean", lm, lb) if lm >= hm else ("k_heavy", hm, hb)
+    gbs = kb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
+    return {"ms": t, "gints_s": units / (t / 1e3) / 1e9,
+            "roofline": {"kernel": kern, "kernel_ms": kms, "alg_bytes": kb, "achieved_gbs": gbs, "frac": gbs / peak,
+                         "lean_ms": lm, "heavy_ms": hm}}
+
+
+def config_legs(rb, args, budget_s=4.0):
+    """Throughput on the plain, sparse and run-heavy workloads (the paper's
+    Sec. 5 pairwise, wide-union and count workloads, synthetic stand-ins),
+    each beside the oracle on every host core and on one core."""
+    import oracle
+    import torch
+    import workloads as W
+    oracle.build()
+    nthr = os.cpu_count() or 1
+    out = {"cpu_model": cpu_model(), "host_threads": nthr}
+
+    def oracle_pair(OA, OB, op, units):
+        def f():
+            r = OA.op(op, OB)
+            r.close()
+            return units
+        return f
+
+    def oracle_jac(OA, OB, units):
+        def f():
+            OA.jaccard(OB)
+            return units
+        return f
+
+    def cpu_legs(tasks):
+        v_all, d_all, s_all = time_tasks(tasks, nthr, budget_s)
+        v_one, d_one, s_one = time_tasks(tasks, 1, budget_s)
+        return {"all_cores": {"gints_s": v_all / 1e9, "cores": nthr, "tasks_done": d_all, "of": len(tasks),
+                              "seconds": s_all},
+                "one_core": {"gints_s": v_one / 1e9, "cores": 1, "tasks_done": d_one, "of": len(tasks),
+                             "seconds": s_one}}
+
+    # plain: AND, OR, ANDNOT, XOR of one pair, materialised, with their counts and Jaccard
+    pool = W.plain_pair(1)
+    va, vb = pool.values(0), pool.values(1)
+    A, B = rb.Bitmap.from_sorted(va), rb.Bitmap.from_sorted(vb)
+    u2 = float(len(va) + len(vb))
+    ops4 = np.arange(4, dtype=np.uint32)
+    pm = rb.Plan([A, B], ops4, np.zeros(4, np.uint32), np.ones(4, np.uint32))
+    leg = plan_leg(rb, pm, 4 * u2)
+    pm.free()
+    calls = []
+    for _ in range(13):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs = [A.op(op, B) for op in range(4)]
+        A.jaccard(B)
+        calls.append(time.perf_counter() - t0)
+        for r in rs:
+            r.free()
+    OA, OB = oracle.Bitmap.from_sorted(va), oracle.Bitmap.from_sorted(vb)
+    tasks = [oracle_pair(OA, OB, op, u2) for op in range(4)] * 8 + [oracle_jac(OA, OB, u2)] * 8
+    out["plain"] = {"what": "AND/OR/ANDNOT/XOR of the two bitmaps, materialised (one plan, 4 queries); "
+                            "units 4 x (|A|+|B|)", "values": int(u2), **leg,
+                    "per_call_gints_s": 4 * u2 / statistics.median(calls[3:]) / 1e9,
+                    "per_call_what": "rb_apply x4 + rb_jaccard, one call at a time, host-synchronous",
+                    "oracle": cpu_legs(tasks)}
+    OA.close(), OB.close(), A.free(), B.free()
+
+    # sparse: AND and OR of the 199 consecutive pairs, and the wide OR of all 200
+    pool = W.make_pool(W.SPECS["sparse"])
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    sz = np.array([len(v) for v in vals], np.float64)
+    a = np.arange(199, dtype=np.uint32)
+    ops = np.concatenate([np.zeros(199, np.uint32), np.ones(199, np.uint32)])
+    aa, bb = np.concatenate([a, a]), np.concatenate([a + 1, a + 1])
+    units = float((sz[aa] + sz[bb]).sum())
+    pm = rb.Plan(G, ops, aa, bb)
+    leg = plan_leg(rb, pm, units)
+    pm.free()
+    wide = []
+    for r in range(8):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m, card = rb.multi_op(1, G)
+        wide.append(time.perf_counter() - t0)
+        m.free()
+    wt = statistics.median(wide[3:])
+    O = [oracle.Bitmap.from_sorted(v) for v in vals]
+
+    def oracle_wide():
+        oracle.Bitmap.multi(1, O).close()
+        return float(sz.sum())
+    tasks = [oracle_pair(O[int(x)], O[int(y)], int(o), float(sz[x] + sz[y])) for o, x, y in zip(ops, aa, bb)]
+    out["sparse"] = {"what": "AND and OR of the 199 consecutive pairs of 200 bitmaps over [0,2^24), c log-uniform "
+                             "1e3..1e6, materialised (one plan, 398 queries)", "values": units, **leg,
+                     "wide_or": {"values": float(sz.sum()), "ms": wt * 1e3, "gints_s": float(sz.sum()) / wt / 1e9,
+                                 "card": int(card), "what": "rb_multi_op(OR) of all 200, host-synchronous call"},
+                     "oracle": cpu_legs(tasks)}
+    t0 = time.perf_counter()
+    oracle_wide()
+    ow = time.perf_counter() - t0
+    out["sparse"]["wide_or"]["oracle_one_core_gints_s"] = float(sz.sum()) / ow / 1e9
+    for o in O:
+        o.close()
+    for g in G:
+        g.free()
+
+    # run-heavy: all four ops of the 199 consecutive pairs, and their Jaccard (count-only)
+    pool = W.make_pool(W.SPECS["runs"])
+    vals = [pool.values(i) for i in range(pool.n)]
+    G = [rb.Bitmap.from_sorted(v) for v in vals]
+    sz = np.array([len(v) for v in vals], np.float64)
+    ops = np.repeat(np.arange(4, dtype=np.uint32), 199)
+    aa, bb = np.tile(a, 4), np.tile(a + 1, 4)
+    units = float((sz[aa] + sz[bb]).sum())
+    pm = rb.Plan(G, ops, aa, bb)
+    leg = plan_leg(rb, pm, units)
+    pm.free()
+    pj = rb.Plan(G, np.zeros(199, np.uint32), a, a + 1, np.full(199, rb.Q_COUNT_ONLY, np.uint32))
+    jleg = plan_leg(rb, pj, float((sz[a] + sz[a + 1]).sum()))
+    pj.free()
+    O = [oracle.Bitmap.from_sorted(v) for v in vals]
+    tasks = [oracle_pair(O[int(x)], O[int(y)], int(o), float(sz[x] + sz[y])) for o, x, y in zip(ops, aa, bb)]
+    jt = [oracle_jac(O[int(x)], O[int(x) + 1], float(sz[x] + sz[x + 1])) for x in a]
+    out["runs"] = {"what": "AND/OR/ANDNOT/XOR of the 199 consecutive pairs of 200 run-heavy bitmaps over [0,2^26), "
+                           "materialised (one plan, 796 queries)", "values": units, **leg,
+                   "jaccard": {"what": "count-only Jaccard of the 199 pairs (one plan)", **jleg,
+                               "oracle": cpu_legs(jt)},
+                   "oracle": cpu_legs(tasks)}
+    for o in O:
+        o.close()
+    for g in G:
+        g.free()
+    return out
+
+
+def serving_on_index(rb, args, rates=(1e3, 1e4, 1e5, 1e6), max_queries=40000):
+    """The serving workload's own index: 10,000 seeded bitmaps (c log-uniform
+    1e2..1e7, 40/30/30 sparse/dense/runs), drawn and uploaded a slice at a
+    time, resident on the device while the load runs."""
+    import torch
+    import workloads as W
+    spec = W.SPECS["serving"]
+    if args.serving_index:
+        spec = W.scaled(spec, n_bitmaps=args.serving_index)
+    t0 = time.time()
+    G = []
+    sizes, cls = W.stream_pool(spec, lambda i, v: G.append(rb.Bitmap.from_sorted(v)))
+    torch.cuda.synchronize()
+    nbytes = sum(g.payload_bytes() + 10 * g.n_containers for g in G)
+    log(f"serving index: {len(G)} bitmaps, {int(sizes.sum()):,} values, {nbytes / 1e9:.2f} GB on the device, "
+        f"built in {time.time() - t0:.1f}s")
+    try:
+        res = serving_leg(rb, G, sizes.astype(np.float64), rates=rates, max_queries=max_queries)
+    finally:
+        for g in G:
+            g.free()
+    res["index"] = (f"{len(G)} bitmaps ({int(sizes.sum()):,} values, {nbytes / 1e9:.2f} GB on the device: "
+                    f"payload + 10 B of key and descriptor per container), c log-uniform 1e2..1e7, "
+                    f"classes {int((cls == 0).sum())}/{int((cls == 1).sum())}/{int((cls == 2).sum())} "
+                    f"sparse/dense/runs")
+    res["index_bytes"] = nbytes
+    return res
+
+
 def serving_leg(rb, G, sizes, rates=(1e3, 1e4, 1e5, 1e6), seconds=2.0, max_queries=40000):
     """Open-loop Poisson load on the serving loop with the pool as its
     resident index: multi-way AND/OR of 2..8 members, materialised or
@@ -502,6 +774,7 @@ def serving_leg(rb, G, sizes, rates=(1e3, 1e4, 1e5, 1e6), seconds=2.0, max_queri
         for rate in rates:
             n = int(min(max_queries, max(200, rate * seconds)))
             ops, ks, co, mem = W.multi_queries(5, n, len(G))
+            reqs = rb.Server.requests(ops, ks, co, mem)   # marshalled before the clock starts
             arrivals = W.poisson_arrivals(5, n, rate)
             units = np.array([float(sizes[mem[i, :ks[i]]].sum()) for i in range(n)])
             tickets = np.zeros(n, np.uint64)
@@ -527,8 +800,7 @@ def serving_leg(rb, G, sizes, rates=(1e3, 1e4, 1e5, 1e6), seconds=2.0, max_queri
                 now = time.perf_counter() - t0
                 j = int(np.searchsorted(arrivals, now, side="right"))
                 if j > i:
-                    tk = srv.submit_many(ops[i:j], ks[i:j], co[i:j], mem[i:j])
-                    tickets[i:j] = tk
+                    srv.submit_prepared(reqs, i, j, tickets)
                     late[i:j] = (time.perf_counter() - t0) - arrivals[i:j]
                     if i == 0:
                         th.start()
@@ -583,7 +855,14 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the library's default schedule")
+    ap.add_argument("--retune", action="store_true", help="tune even if the schedule cache has an entry")
+    ap.add_argument("--schedule-cache", default=os.environ.get("RB_SCHEDULE_CACHE", os.path.join(
+        os.environ.get("XDG_CACHE_HOME", os.path.expanduser("~/.cache")), "gbroaring", "schedules.json")),
+        help="JSON schedule cache keyed by GPU name and workload")
+    ap.add_argument("--no-configs", action="store_true", help="skip the plain / sparse / run-heavy legs")
+    ap.add_argument("--serving-index", type=int, default=0,
+                    help="scaled case: bitmaps of the serving index (default: the full 10,000)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-subsets", action="store_true", help="skip the bitset-dominated AND/OR legs")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")

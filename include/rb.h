@@ -253,8 +253,16 @@ typedef struct {
 rb_status rb_set_schedule(const rb_schedule *s);
 rb_status rb_get_schedule(rb_schedule *s);
 
-/* Time every candidate schedule on the plan (reps runs each, CUDA events),
- * install the fastest as the current schedule and return it. */
+/* Tune the schedule on the plan (no paper counterpart): coordinate descent
+ * from the current schedule over the heavy kernel's shape ({2,6}, {4,3},
+ * {8,1} warps per CTA x CTAs per SM), small_intervals (32, 48, 64, 96, 128),
+ * lean_ctas_per_sm (6, 7, 8) and prefetch_lines (0, 2, 4, 8): each pass
+ * times every value of one knob with the others fixed (one warm-up run,
+ * then reps runs, CUDA events on `stream`, key merge + container-pair
+ * kernels) and keeps the fastest, until a pass changes nothing (at most 3
+ * passes).  The fastest is installed as the current schedule and returned
+ * in *best with its time in *best_ms.  Results do not depend on the
+ * schedule. */
 rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *best,
                       double *best_ms);
 
@@ -362,7 +370,9 @@ void rb_server_destroy(rb_server_t *s);
  * does cap below the cardinality.  Every call on a device shares that array:
  * calls whose work overlaps on the device race.  The first call on each
  * device looks up the array's device address (set-up, with that device
- * current); make that first call before any stream capture.  The call only
+ * current); make that first call before any stream capture.  After a
+ * cudaDeviceReset the array may be reloaded elsewhere: the next call on that
+ * device sees the new context and repeats the set-up.  The call only
  * enqueues work on `stream`: the values are in dst once the stream reaches
  * it.  RB_ECUDA if a CUDA call fails. */
 rb_status rb_to_u32_noalloc(const rb_t *b, uint32_t *dst, uint64_t cap, uint64_t *n_out, void *stream);

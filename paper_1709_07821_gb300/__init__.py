@@ -625,24 +625,46 @@ class Server:
         _check(lib().rb_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         return t.value
 
+    @staticmethod
+    def requests(ops, ks, count_only, members) -> np.ndarray:
+        """n requests marshalled as rb_request records (one row of
+        3 + SERVE_MAX_K uint32 each: op, k, count_only, members), for
+        submit_many and submit_prepared."""
+        n = len(ops)
+        mem = np.asarray(members, dtype=np.int64).reshape(n, -1) if n else np.zeros((0, SERVE_MAX_K), np.int64)
+        arr = np.zeros((max(1, n), 3 + SERVE_MAX_K), np.uint32)
+        if n:
+            arr[:n, 0] = _u32(ops, "ops")
+            arr[:n, 1] = _u32(ks, "k")
+            arr[:n, 2] = (np.asarray(count_only) != 0).astype(np.uint32)
+            w = min(SERVE_MAX_K, mem.shape[1])
+            # members past k are not read by the library; keep them in range
+            arr[:n, 3:3 + w] = np.where(mem[:, :w] < 0, 0, mem[:, :w] & 0xFFFFFFFF).astype(np.uint32)
+        assert ctypes.sizeof(Request) == arr.shape[1] * 4
+        return arr
+
+    def submit_prepared(self, reqs: np.ndarray, lo: int, hi: int, tickets: np.ndarray):
+        """Queue rows lo..hi of a marshalled request array (Server.requests)
+        in one call; tickets[lo:hi] (a uint64 array) receive their tickets."""
+        if hi <= lo:
+            return
+        if not (reqs.flags.c_contiguous and reqs.dtype == np.uint32 and tickets.dtype == np.uint64
+                and hi <= len(reqs) and hi <= len(tickets) and lo >= 0):
+            raise ValueError("submit_prepared: bad request or ticket array")
+        row = reqs.shape[1] * 4
+        _check(lib().rb_server_submit_many(self._h, ctypes.cast(ctypes.c_void_p(reqs.ctypes.data + lo * row),
+                                                                ctypes.POINTER(Request)), hi - lo,
+                                           ctypes.cast(ctypes.c_void_p(tickets.ctypes.data + 8 * lo),
+                                                       ctypes.POINTER(ctypes.c_uint64))))
+
     def submit_many(self, ops, ks, count_only, members) -> np.ndarray:
         """Queue n requests in one call: ops[i], ks[i] members from row i of
         members (an n x SERVE_MAX_K array), count_only[i]; returns the
         tickets (uint64)."""
         n = len(ops)
-        reqs = (Request * max(1, n))()
-        mem = np.asarray(members)
-        for i in range(n):
-            r = reqs[i]
-            r.op = int(ops[i])
-            r.k = int(ks[i])
-            r.count_only = 1 if count_only[i] else 0
-            for j in range(min(int(ks[i]), SERVE_MAX_K)):
-                r.members[j] = int(mem[i, j])
         t = np.zeros(max(1, n), np.uint64)
         if n:
-            _check(lib().rb_server_submit_many(self._h, reqs, n,
-                                               t.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+            self.submit_prepared(self.requests(ops, ks, count_only, members), 0, n, t)
         return t[:n]
 
     def poll(self, cap: int = 1024, timeout_ms: int = 100, want_bitmaps: bool = False):

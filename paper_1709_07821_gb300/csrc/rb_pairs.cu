@@ -2164,31 +2164,70 @@ rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *be
     if (reps == 0) reps = 1;
     cudaStream_t s = (cudaStream_t)stream;
     const rb_schedule saved = current_schedule();
-    static const uint32_t heavy[][2] = {{2, 6}, {4, 3}, {8, 1}};
-    static const uint32_t smalls[] = {64, 256, 512};
-    static const uint32_t leans[] = {4, LEAN_CTAS_MAX};
-    rb_schedule win = saved;
-    double win_ms = 1e30;
     std::vector<rb_t *> outs(p->q.size(), nullptr);
-    for (auto &sh : heavy) {
-        for (uint32_t sm : smalls) {
-            for (uint32_t ln : leans) {
-                rb_schedule c = {sh[0], sh[1], sm, ln, saved.prefetch_lines};
-                if (rb_set_schedule(&c) != RB_OK) continue;
-                double tot = 0;
-                bool ok = true;
-                for (uint32_t r = 0; r < reps + 1 && ok; r++) {
-                    rb_status st = plan_execute(p, outs.data(), nullptr, s, false);
-                    for (auto &h : outs) { rb_free(h); h = nullptr; }
-                    if (st != RB_OK) ok = false;
-                    else if (r > 0) tot += p->last_ms;   // the first run is a warm-up
-                }
-                if (ok && tot / reps < win_ms) {
-                    win_ms = tot / reps;
-                    win = c;
-                }
-            }
+    // mean kernel time of reps runs after one warm-up run (CUDA events on
+    // the launching stream, key merge + container-pair stages); < 0 if the
+    // schedule does not run
+    auto measure = [&](const rb_schedule &c) -> double {
+        if (rb_set_schedule(&c) != RB_OK) return -1.0;
+        double tot = 0;
+        for (uint32_t r = 0; r < reps + 1; r++) {
+            const rb_status st = plan_execute(p, outs.data(), nullptr, s, false);
+            for (auto &h : outs) { rb_free(h); h = nullptr; }
+            if (st != RB_OK) return -1.0;
+            if (r > 0) tot += p->last_ms;
         }
+        return tot / reps;
+    };
+    // Coordinate descent from the current schedule over the knobs that
+    // change the kernels' speed: the heavy kernel's shape (warps per CTA x
+    // CTAs per SM), the largest array pair one lane merges alone (larger
+    // ones go to 8-lane groups), the lean kernel's CTAs per SM and the L2
+    // prefetch depth.  Each pass tries every value of one knob with the
+    // others fixed and keeps the fastest; it stops after a pass that
+    // changes nothing (at most three passes).
+    static const uint32_t heavy[][2] = {{2, 6}, {4, 3}, {8, 1}};
+    static const uint32_t smalls[] = {32, 48, 64, 96, 128};
+    static const uint32_t leans[] = {6, 7, LEAN_CTAS_MAX};
+    static const uint32_t prefs[] = {0, 2, 4, 8};
+    rb_schedule win = saved;
+    if (win.lean_ctas_per_sm == 0) win.lean_ctas_per_sm = LEAN_CTAS_MAX;
+    double win_ms = measure(win);
+    if (win_ms < 0) win_ms = 1e30;
+    auto consider = [&](const rb_schedule &c) -> bool {
+        if (memcmp(&c, &win, sizeof c) == 0) return false;
+        const double ms = measure(c);
+        if (ms >= 0 && ms < win_ms) {
+            win_ms = ms;
+            win = c;
+            return true;
+        }
+        return false;
+    };
+    for (int pass = 0; pass < 3; pass++) {
+        bool changed = false;
+        for (auto &h : heavy) {
+            rb_schedule c = win;
+            c.warps_per_cta = h[0];
+            c.ctas_per_sm = h[1];
+            changed |= consider(c);
+        }
+        for (uint32_t v : smalls) {
+            rb_schedule c = win;
+            c.small_intervals = v;
+            changed |= consider(c);
+        }
+        for (uint32_t v : leans) {
+            rb_schedule c = win;
+            c.lean_ctas_per_sm = v;
+            changed |= consider(c);
+        }
+        for (uint32_t v : prefs) {
+            rb_schedule c = win;
+            c.prefetch_lines = v;
+            changed |= consider(c);
+        }
+        if (!changed) break;
     }
     rb_set_schedule(win_ms < 1e30 ? &win : &saved);
     if (best) *best = current_schedule();
