@@ -217,18 +217,22 @@ rb_status rb_plan_run(rb_plan_t *p, rb_t **outs, uint64_t *counts, void *stream)
 rb_status rb_plan_launch(rb_plan_t *p, void *stream);
 rb_status rb_plan_collect(rb_plan_t *p, rb_t **outs, uint64_t *counts);
 /* Measurements of the last run, from CUDA events on the stream the kernels
- * ran on: the container-pair stage is a lean kernel (key merge, small pairs)
- * then a heavy kernel (pairs deferred by the lean one: bitsets, many values
- * or runs).  *_bytes are the algorithmic bytes of each kernel's share of the
- * work: the input payloads the op must read (AND: matched containers; OR,
- * XOR: every container; ANDNOT: all of a, matched of b) and the output
- * payloads, counted by the kernels themselves, plus 15 bytes of key and
- * metadata per container of both inputs (lean kernel) and per output
- * container, and 8 bytes per count-only result; deferred is the number of
- * deferred pairs. */
+ * ran on: the container-pair stage is a lean kernel (key merge, copies of
+ * unmatched containers), a small-pair kernel (the array pairs and small run
+ * pairs the lean one queued) and a heavy kernel (pairs with a bitset, many
+ * values or many runs, and bitset copies).  *_bytes are the algorithmic
+ * bytes of each kernel's share of the work: the input payloads the op must
+ * read (AND: matched containers; OR, XOR: every container; ANDNOT: all of
+ * a, matched of b) and the output payloads, counted by the kernels
+ * themselves, plus 15 bytes of key and metadata per container of both
+ * inputs (lean kernel) and per output container, and 8 bytes per
+ * count-only result; deferred and small_pairs are the numbers of pairs
+ * queued for the heavy and the small-pair kernel. */
 typedef struct {
     double lean_ms, heavy_ms;
     uint64_t lean_bytes, heavy_bytes, alg_bytes, out_bytes, deferred;
+    double small_ms;
+    uint64_t small_bytes, small_pairs;
 } rb_plan_timing;
 rb_status rb_plan_stats(const rb_plan_t *p, rb_plan_timing *t);
 void rb_plan_free(rb_plan_t *p);

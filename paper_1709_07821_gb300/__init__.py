@@ -49,7 +49,8 @@ class Schedule(ctypes.Structure):
 class PlanTiming(ctypes.Structure):
     _fields_ = [("lean_ms", ctypes.c_double), ("heavy_ms", ctypes.c_double), ("lean_bytes", ctypes.c_uint64),
                 ("heavy_bytes", ctypes.c_uint64), ("alg_bytes", ctypes.c_uint64), ("out_bytes", ctypes.c_uint64),
-                ("deferred", ctypes.c_uint64)]
+                ("deferred", ctypes.c_uint64), ("small_ms", ctypes.c_double), ("small_bytes", ctypes.c_uint64),
+                ("small_pairs", ctypes.c_uint64)]
 
 
 class Request(ctypes.Structure):
@@ -484,9 +485,10 @@ class Plan:
     def stats(self):
         t = PlanTiming()
         _check(lib().rb_plan_stats(self._h, ctypes.byref(t)))
-        return {"lean_ms": t.lean_ms, "heavy_ms": t.heavy_ms, "kernel_ms": t.lean_ms + t.heavy_ms,
-                "lean_bytes": t.lean_bytes, "heavy_bytes": t.heavy_bytes, "alg_bytes": t.alg_bytes,
-                "out_bytes": t.out_bytes, "deferred": t.deferred}
+        return {"lean_ms": t.lean_ms, "small_ms": t.small_ms, "heavy_ms": t.heavy_ms,
+                "kernel_ms": t.lean_ms + t.small_ms + t.heavy_ms, "lean_bytes": t.lean_bytes,
+                "small_bytes": t.small_bytes, "heavy_bytes": t.heavy_bytes, "alg_bytes": t.alg_bytes,
+                "out_bytes": t.out_bytes, "deferred": t.deferred, "small_pairs": t.small_pairs}
 
     def autotune(self, reps=2, stream=None):
         s = Schedule()

@@ -75,6 +75,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return mbar_wait_for(bar, parity, MBAR_WAIT_CYCLES);
 }
 
+// 4 bytes from global to shared memory without holding a register
+// (cp.async, Ampere onward); every copy a thread issued is complete once it
+// has run cp_async_wait_all, which waits like a load does (no spin)
+__device__ __forceinline__ void cp_async4(void *dst_smem, const void *src_gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst_smem)), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
 #pragma unroll
     for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(FULL, x, d);

@@ -20,12 +20,13 @@
 //
 // Kernels.  k_lean (high occupancy, small shared buffers) does the key merge
 // of a tile, copies the tile's unmatched array and run containers with the
-// whole warp, and queues its container pairs; each batch of 32 queued pairs
-// is finished one pair per lane (small array merges, run sweeps) or by the
-// whole warp in turn (array pairs up to 1024 values).  Pairs with a bitset or
-// more values go to a deferred queue that k_heavy (one warp per pair, two
-// 8 KB shared tiles per warp, bitsets moved by bulk copies) drains.
-// k_compact then drops the empty results of every query.
+// whole warp, and queues its container pairs.  Small pairs go to the
+// small-pair queue that k_small drains 32 at a time: one pair per lane (small
+// array merges, run sweeps) or by groups of 8 lanes or the whole warp in turn
+// (array pairs up to 1024 values).  Pairs with a bitset or more values go to
+// a deferred queue that k_heavy (one warp per pair, two 8 KB shared tiles per
+// warp, bitsets moved by bulk copies) drains.  k_compact then drops the empty
+// results of every query.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -41,9 +42,7 @@ namespace {
 constexpr uint32_t F_COUNT = 1, F_MERGE = 2;
 enum : uint32_t { K_NONE = 0, K_EMPTY = 1, K_PAIR = 2, K_COPY_A = 3, K_COPY_B = 4 };
 constexpr int LEAN_THREADS = 128;
-// resident k_lean CTAs per SM: a bound of 64 registers per thread (40 bytes
-// of spills) and 21.7 KB of shared memory per CTA, which leaves about 60 KB
-// of each SM's L1 for the one-lane merges' payload streams
+// resident k_lean CTAs per SM (a bound of 64 registers per thread)
 constexpr uint32_t LEAN_CTAS_MAX = 8;
 constexpr uint32_t KEY_END = 0x10000u;   // past-the-end key sentinel
 // algorithmic bytes of a container's key and metadata (key 2, type 1,
@@ -70,15 +69,30 @@ struct Deferred {
     uint32_t kind_key, pad;
 };
 
+// a container pair for the small-pair kernel (one-lane, 8-lane group or
+// warp merges and run sweeps)
+struct Item {
+    unsigned long long da, db;
+    uint32_t p, pos;
+    uint32_t info;   // key | kind << 16 | mode << 20
+    uint32_t pad;
+};
+
+// Run state in device memory.  The small-pair queue small[0, small_cap)
+// holds the one-lane items from index 0 up (small_n1 of them) and the
+// group and warp items from the top down (small_n2); the small-pair kernel
+// checks small_n1 + small_n2 <= small_cap before it reads any item.
 struct ExecState {
     uint8_t *arena;
     uint16_t *keys;
     uint64_t *descs;
     Deferred *defer;
+    Item *small;
     unsigned long long words_off, words_cap, bits_off, bits_cap;
     unsigned long long words_used, bits_used, work, hwork;
     unsigned long long defer_cap, defer_n;
-    unsigned long long lean_bytes, heavy_bytes;
+    unsigned long long small_cap, small_n1, small_n2, swork1, swork2;
+    unsigned long long lean_bytes, heavy_bytes, small_bytes;
     unsigned int status, pad;
 };
 
@@ -332,7 +346,8 @@ __device__ __forceinline__ uint32_t keep_table(uint32_t op) {
 // one lane merges two small sorted arrays without branches on the data: each
 // step takes the smaller head (a first on a tie), notes whether the other
 // input holds it, and keeps it by the op's table; counts cardinality c and
-// runs r, and with EMIT writes the kept values
+// runs r, and with EMIT writes the kept values.  a and b are generic
+// pointers: the arrays staged in shared memory, or in global memory.
 template <bool EMIT>
 __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *a, uint32_t na, const uint16_t *b,
                                                   uint32_t nb, uint32_t &c, uint32_t &r, uint16_t *out) {
@@ -345,8 +360,8 @@ __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *
     const bool keep_a_rest = (tbl & 4u) != 0, keep_b_rest = (tbl & 1u) != 0;
 #pragma unroll 1
     while ((i < na && (j < nb || keep_a_rest)) || (j < nb && keep_b_rest)) {
-        const uint32_t va = i < na ? (uint32_t)__ldg(a + i) : KEY_END;
-        const uint32_t vb = j < nb ? (uint32_t)__ldg(b + j) : KEY_END;
+        const uint32_t va = i < na ? (uint32_t)a[i] : KEY_END;
+        const uint32_t vb = j < nb ? (uint32_t)b[j] : KEY_END;
         const bool ta = va <= vb;
         const uint32_t v = ta ? va : vb;
         const bool ino = ta ? (vb == va) : (pa == vb);
@@ -377,15 +392,7 @@ constexpr uint32_t WARP_MERGE_MAX = 1024;   // values of both arrays the warp me
 constexpr uint32_t GW = 8, GSEG = 256, GPER = 32 / GW;
 constexpr uint32_t GRP_MAX = GSEG - 2;
 constexpr uint32_t RUN_SWEEP_MAX = 512;     // intervals one lane sweeps when runs are involved
-constexpr uint32_t QCAP = 64;               // container pairs queued per warp
-
-// a container pair waiting in a warp's queue
-struct Item {
-    unsigned long long da, db;
-    uint32_t p, pos;
-    uint32_t info;   // key | kind << 16 | mode << 20
-    uint32_t pad;
-};
+constexpr uint32_t LSTG_WORDS = WARP_MERGE_MAX;   // 4-byte words of the staging area (4 KB)
 
 // bytes reserved for an array-by-array result before it is computed: the
 // array encoding of the largest possible result (the run encoding, chosen
@@ -553,11 +560,77 @@ __device__ __noinline__ void queue_deferred(ExecState *es, uint32_t lm, bool min
     }
 }
 
+// Small-pair queue slots are taken SQCHUNK at a time from the shared
+// counters; each warp hands out its current block ([qs[0], qs[1]) for
+// one-lane items, [qs[2], qs[3]) for the others) and moves to a new block in
+// the middle of a tile when one runs out, so that the only unused slots are
+// the rest of each warp's last blocks, which k_lean fills with no-op items
+// before it ends.
+constexpr uint32_t SQCHUNK = 256;
+__device__ __forceinline__ unsigned long long sq_take(unsigned long long *ctr, unsigned long long *qs, uint32_t cnt,
+                                                      uint32_t k, uint32_t lane) {
+    const unsigned long long cur = qs[0], end = qs[1], rem = end - cur;
+    unsigned long long nb = 0;
+    if (cnt > rem) {
+        if (lane == 0) nb = atomicAdd(ctr, (unsigned long long)SQCHUNK);
+        nb = __shfl_sync(FULL, nb, 0);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        if (cnt > rem) {
+            qs[0] = nb + (cnt - rem);
+            qs[1] = nb + SQCHUNK;
+        } else {
+            qs[0] = cur + cnt;
+        }
+    }
+    __syncwarp();
+    return k < rem ? cur + k : nb + (k - rem);
+}
+
+// append the tile's small container pairs (lanes in am) to the small-pair
+// queue: one-lane items (one1) from the bottom, the others from the top
+__device__ __noinline__ void queue_small(ExecState *es, unsigned long long *qs, uint32_t am, bool mine, bool one1,
+                                         uint64_t da, uint64_t db, uint32_t p, uint32_t pos, uint32_t info,
+                                         uint32_t lane) {
+    const uint32_t m1 = __ballot_sync(FULL, mine && one1), m2 = am & ~m1;
+    unsigned long long k1 = 0, k2 = 0;
+    if (m1) k1 = sq_take(&es->small_n1, qs, __popc(m1), __popc(m1 & lanemask_lt(lane)), lane);
+    if (m2) k2 = sq_take(&es->small_n2, qs + 2, __popc(m2), __popc(m2 & lanemask_lt(lane)), lane);
+    if (mine) {
+        const unsigned long long k = one1 ? k1 : k2;
+        if (k < es->small_cap) {
+            Item it;
+            it.da = da;
+            it.db = db;
+            it.p = p;
+            it.pos = pos;
+            it.info = info;
+            it.pad = 0;
+            es->small[one1 ? k : es->small_cap - 1 - k] = it;
+        } else {
+            atomicOr(&es->status, 2u);
+        }
+    }
+}
+
+// no-op items in the unused rest of a warp's blocks (mode M_NONE)
+__device__ __noinline__ void sq_close(ExecState *es, const unsigned long long *qs, uint32_t lane) {
+    for (int c = 0; c < 2; c++) {
+        for (unsigned long long k = qs[2 * c] + lane; k < qs[2 * c + 1]; k += 32) {
+            if (k >= es->small_cap) break;
+            Item it;
+            it.da = it.db = 0;
+            it.p = it.pos = it.info = it.pad = 0;
+            es->small[c == 0 ? k : es->small_cap - 1 - k] = it;
+        }
+    }
+}
+
 // Key merge of one tile: each lane resolves its slot into a container pair,
 // an empty result, a copy or nothing.  Empty results and copies of array and
 // run containers are finished at once, pairs with a bitset or many values go
-// to the heavy kernel's queue, and the others are appended to the warp's item
-// queue q (qn stays warp-uniform).
+// to the heavy kernel's queue, and the others to the small-pair queue.
 //
 // Tiles come in chunks of consecutive ones, and the cursor carries what the
 // previous tile found: its query's tile range, so that the query is looked up
@@ -569,8 +642,8 @@ struct TileCursor {
     uint32_t p, i_next;
 };
 
-__device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCursor &cur, uint32_t *win, Item *q,
-                             uint32_t &qn, unsigned long long *wa, unsigned long long &meta, uint32_t lane) {
+__device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCursor &cur, uint32_t *win,
+                             unsigned long long *wa, unsigned long long &meta, uint32_t lane) {
     if (t < cur.lo || t >= cur.hi) {
         flush_sums(P.stats, cur.p, wa, lane);
         uint32_t lo = 0, hi = P.n_pairs;
@@ -691,18 +764,8 @@ __device__ void resolve_tile(const PairParams &P, unsigned long long t, TileCurs
         prefetch_payload(B.base + d_off(db), in_payload_bytes(db), P.prefetch);
     }
     const uint32_t am = __ballot_sync(FULL, act);
-    if (act) {
-        Item it;
-        it.da = da;
-        it.db = db;
-        it.p = p;
-        it.pos = pos;
-        it.info = key | (kind << 16) | (mode << 20);
-        it.pad = 0;
-        q[qn + __popc(am & lanemask_lt(lane))] = it;
-    }
-    qn += __popc(am);
-    __syncwarp();
+    if (am) queue_small(es, wa + 4, am, act, mode == M_LANE_ARR || mode == M_LANE_SWEEP, da, db, p, pos,
+                        key | (kind << 16) | (mode << 20), lane);
 }
 
 // The first 32 four-byte words of both arrays of a warp-sized pair, one per
@@ -1119,18 +1182,18 @@ __device__ __noinline__ void process_warp_merges(ExecState *es, uint32_t wq, con
     }
 }
 
-// Process n <= 32 queued container pairs, one per lane (warp-sized ones by
-// the whole warp in turn), with one allocation for all their outputs.  The
-// queue holds pairs only: copies are done during the key merge.
+// Process n <= 32 queued container pairs q[0, n), one per lane (group- and
+// warp-sized ones by 8 lanes or the whole warp in turn), with one allocation
+// for all their outputs.  The queue holds pairs only: copies are done during
+// the key merge.  stg is the warp's 4 KB staging area.
 __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, uint16_t *stg, unsigned long long *wa,
                               unsigned long long &bytes_acc, uint32_t lane) {
     ExecState *es = P.es;
-    const bool has = lane < n;
     Item it;
     it.da = it.db = 0;
     it.p = it.pos = it.info = it.pad = 0;
-    if (has) it = q[lane];
-    __syncwarp();   // the items are read before the staging area (queue slots 32..63) is written
+    if (lane < n) it = q[lane];
+    const bool has = lane < n && ((it.info >> 20) & 7u) != M_NONE;   // no-op items fill unused queue slots
     const uint32_t mode = has ? (it.info >> 20) & 7u : M_NONE;
     const uint32_t key = it.info & 0xFFFFu;
     const PairDev pd = P.pairs[it.p];
@@ -1139,6 +1202,29 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     const uint32_t op = count ? (uint32_t)OP_AND : pd.op;
     const uint32_t tbl = keep_table(op);
     const CRef ca = cref(abase, it.da), cb = cref(bbase, it.db);
+
+    // One-lane array merges read both arrays from the warp's staging area:
+    // every lane's words are requested at once (cp.async), so the warp waits
+    // for one memory latency, not once for every cache line a lane reaches
+    // (the lines of 32 lanes' arrays do not stay in L1 at this occupancy).
+    // Lanes whose words would pass the end of the area read global memory.
+    const uint16_t *la = reinterpret_cast<const uint16_t *>(ca.p), *lb = reinterpret_cast<const uint16_t *>(cb.p);
+    if (__any_sync(FULL, mode == M_LANE_ARR)) {
+        const uint32_t wa = mode == M_LANE_ARR ? (ca.card + 1) / 2 : 0, wb = mode == M_LANE_ARR ? (cb.card + 1) / 2 : 0;
+        const uint32_t wincl = warp_incl(wa + wb, lane);
+        if (mode == M_LANE_ARR && wincl <= LSTG_WORDS) {
+            uint32_t *S = reinterpret_cast<uint32_t *>(stg) + (wincl - wa - wb);
+            const uint32_t *A32 = reinterpret_cast<const uint32_t *>(ca.p), *B32 = reinterpret_cast<const uint32_t *>(cb.p);
+#pragma unroll 1
+            for (uint32_t k = 0; k < wa; k++) cp_async4(S + k, A32 + k);
+#pragma unroll 1
+            for (uint32_t k = 0; k < wb; k++) cp_async4(S + wa + k, B32 + k);
+            la = reinterpret_cast<const uint16_t *>(S);
+            lb = reinterpret_cast<const uint16_t *>(S + wa);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+    }
 
     // sizes: exact for run sweeps, the array bound for array merges
     uint32_t bytes = 0, lc = 0, lr = 0, lt = 0;
@@ -1168,12 +1254,9 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     if (mode == M_LANE_ARR) {
         uint32_t c, r;
         if (count || off == ALLOC_FAIL) {
-            lane_merge_arrays<false>(tbl, reinterpret_cast<const uint16_t *>(ca.p), ca.card,
-                                     reinterpret_cast<const uint16_t *>(cb.p), cb.card, c, r, nullptr);
+            lane_merge_arrays<false>(tbl, la, ca.card, lb, cb.card, c, r, nullptr);
         } else {
-            lane_merge_arrays<true>(tbl, reinterpret_cast<const uint16_t *>(ca.p), ca.card,
-                                    reinterpret_cast<const uint16_t *>(cb.p), cb.card, c, r,
-                                    reinterpret_cast<uint16_t *>(es->arena + off));
+            lane_merge_arrays<true>(tbl, la, ca.card, lb, cb.card, c, r, reinterpret_cast<uint16_t *>(es->arena + off));
             if (c) {
                 const uint32_t ty = canon_type(c, r);
                 if (ty == T_RUN) {   // rare: rewrite the reserved space as runs
@@ -1195,6 +1278,7 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
             card = lc;
         }
     }
+    __syncwarp();   // the staging area is free again
     // group-sized array merges, GPER at a time
     const uint32_t gq = __ballot_sync(FULL, mode == M_GRP_ARR);
     if (gq) process_groups(es, gq, ca, cb, tbl, off, count, stg, lane, desc, card);
@@ -1221,48 +1305,66 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
 
 __global__ void __launch_bounds__(LEAN_THREADS, LEAN_CTAS_MAX) k_lean(PairParams P) {
     __shared__ uint32_t s_win[LEAN_THREADS / 32][66];
-    // per warp: the item queue, whose upper half (slots 32..63) is also the
-    // start of the merge staging area: the upper slots are filled only while
-    // a tile is resolved, and process_items reads its items into registers
-    // before it stages anything, while at most 31 items (slots 0..30) wait
-    static_assert(QCAP == 64 && sizeof(Item) == 32, "queue slot 32 starts the staging area");
-    __shared__ __align__(16) uint8_t s_wq[LEAN_THREADS / 32][(QCAP / 2) * sizeof(Item) + 4 * WARP_MERGE_MAX];
-    __shared__ unsigned long long s_alloc[LEAN_THREADS / 32][4];
+    // per warp: word-region chunk and query sums (0..3), small-queue blocks (4..7)
+    __shared__ unsigned long long s_alloc[LEAN_THREADS / 32][8];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Item *q = reinterpret_cast<Item *>(s_wq[warp]);
-    uint16_t *stg = reinterpret_cast<uint16_t *>(s_wq[warp] + (QCAP / 2) * sizeof(Item));
-    if (lane == 0) s_alloc[warp][0] = s_alloc[warp][1] = s_alloc[warp][2] = s_alloc[warp][3] = 0;
+    if (lane < 8) s_alloc[warp][lane] = 0;
     __syncwarp();
-    uint32_t qn = 0;
-    bool done = false;
     unsigned long long bytes_acc = 0, t = 0, t_end = 0;
     TileCursor cur;
     cur.lo = cur.hi = 0;
     cur.t_next = ~0ull;
     cur.p = cur.i_next = 0;
     for (;;) {
-        while (qn < 32 && !done) {
-            if (t == t_end) {
-                if (lane == 0) t = atomicAdd(&P.es->work, (unsigned long long)P.chunk);
-                t = __shfl_sync(FULL, t, 0);
-                if (t >= P.n_tiles) {
-                    done = true;
-                    break;
-                }
-                t_end = min(t + P.chunk, P.n_tiles);
-            }
-            resolve_tile(P, t, cur, s_win[warp], q, qn, s_alloc[warp], bytes_acc, lane);
-            t++;
+        if (t == t_end) {
+            if (lane == 0) t = atomicAdd(&P.es->work, (unsigned long long)P.chunk);
+            t = __shfl_sync(FULL, t, 0);
+            if (t >= P.n_tiles) break;
+            t_end = min(t + P.chunk, P.n_tiles);
         }
-        if (qn == 0) break;
-        const uint32_t take = qn < 32 ? qn : 32;
-        process_items(P, q + (qn - take), take, stg, s_alloc[warp], bytes_acc, lane);
-        qn -= take;
-        __syncwarp();
+        resolve_tile(P, t, cur, s_win[warp], s_alloc[warp], bytes_acc, lane);
+        t++;
     }
+    sq_close(P.es, s_alloc[warp] + 4, lane);
     flush_sums(P.stats, cur.p, s_alloc[warp], lane);
     const unsigned long long tot = warp_sum64(bytes_acc);
     if (lane == 0 && tot) atomicAdd(&P.es->lean_bytes, tot);
+}
+
+// ------------------------------------------------------------ small-pair kernel
+
+// The small container pairs k_lean queued, by a persistent kernel whose warps
+// take 32 queued pairs at a time: first every one-lane item (array merges of
+// at most small_iv values, run sweeps), then the group and warp items (array
+// pairs merged by 8 lanes, four at once, or by the whole warp).  All warps
+// work through one phase before the next, so each phase's code stays hot.
+constexpr uint32_t SMALL_CTAS_MAX = 8;
+__global__ void __launch_bounds__(LEAN_THREADS, SMALL_CTAS_MAX) k_small(PairParams P) {
+    __shared__ __align__(16) uint16_t s_stg[LEAN_THREADS / 32][2 * WARP_MERGE_MAX];
+    __shared__ unsigned long long s_alloc[LEAN_THREADS / 32][4];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ExecState *es = P.es;
+    if (lane == 0) s_alloc[warp][0] = s_alloc[warp][1] = s_alloc[warp][2] = s_alloc[warp][3] = 0;
+    __syncwarp();
+    const unsigned long long cap = es->small_cap, n1 = es->small_n1, n2 = es->small_n2;
+    if (n1 + n2 > cap) return;   // the queue overflowed: the host reruns with exact sizes
+    unsigned long long bytes_acc = 0;
+    bool second = false;   // phase: one-lane items, then group and warp items
+    for (;;) {
+        const unsigned long long n = second ? n2 : n1;
+        unsigned long long x = 0;
+        if (lane == 0) x = atomicAdd(second ? &es->swork2 : &es->swork1, 32ull);
+        x = __shfl_sync(FULL, x, 0);
+        if (x >= n) {
+            if (second) break;
+            second = true;
+            continue;
+        }
+        process_items(P, es->small + (second ? cap - n2 : 0ull) + x, (uint32_t)min(32ull, n - x), s_stg[warp],
+                      s_alloc[warp], bytes_acc, lane);
+    }
+    const unsigned long long tot = warp_sum64(bytes_acc);
+    if (lane == 0 && tot) atomicAdd(&es->small_bytes, tot);
 }
 
 // ------------------------------------------------------------ heavy kernel
@@ -1545,6 +1647,7 @@ struct rb_plan {
     std::vector<PairDev> pairs;
     uint64_t total_pos = 0, total_tiles = 0;
     uint64_t words_cap = 0, bits_cap = 0, defer_cap = 0;   // arena sizes for the next run
+    uint64_t small_cap = 0;                                // small-pair queue entries for the next run
     bool exact = false;                                    // caps measured by a previous run
     bool any_mat = false;
     uint8_t *tables = nullptr;
@@ -1558,14 +1661,15 @@ struct rb_plan {
     PairStats *h_stats = nullptr;
     ExecState *h_es = nullptr;
     cudaStream_t ps = nullptr;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev_in = nullptr, ev_done = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr, ev_in = nullptr, ev_done = nullptr;
     RbArena *pending = nullptr;   // result memory of a run launched by rb_plan_launch, not yet collected
     bool pending_graph = false;
     cudaStream_t pending_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     rb_schedule gsched = {0, 0, 0, 0, 0};
-    double last_ms = 0, last_lean_ms = 0, last_heavy_ms = 0;
-    uint64_t last_alg = 0, last_out = 0, last_lean_bytes = 0, last_heavy_bytes = 0, last_deferred = 0;
+    double last_ms = 0, last_lean_ms = 0, last_small_ms = 0, last_heavy_ms = 0;
+    uint64_t last_alg = 0, last_out = 0, last_lean_bytes = 0, last_small_bytes = 0, last_heavy_bytes = 0;
+    uint64_t last_deferred = 0, last_small = 0;
     uint64_t meta_bytes = 0;   // algorithmic key + metadata bytes of the inputs (and count results)
     cudaStream_t alloc_stream = nullptr;
 };
@@ -1581,6 +1685,7 @@ void plan_destroy(rb_plan *p) {
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     if (p->ev2) cudaEventDestroy(p->ev2);
+    if (p->ev3) cudaEventDestroy(p->ev3);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_done) cudaEventDestroy(p->ev_done);
     if (p->pending) {
@@ -1607,6 +1712,8 @@ void query_bounds(const rb *A, const rb *B, uint32_t op, uint64_t &w, uint64_t &
     bits = 8192ull * std::min<uint64_t>(slots, cards / 4097 + 1);
 }
 
+uint64_t lean_warps(const rb_plan *p, const rb_schedule &sc);
+
 rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q, uint64_t nq, cudaStream_t s,
                      bool use_bounds, rb_plan **out) {
     *out = nullptr;
@@ -1620,7 +1727,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     p->q.assign(q, q + nq);
     p->pairs.resize(nq);
     std::vector<unsigned long long> tb(nq + 1);
-    uint64_t npos = 0, tiles = 0, ew = 0, eb = 0, bw = 0, bb = 0, ed = 0;
+    uint64_t npos = 0, tiles = 0, ew = 0, eb = 0, bw = 0, bb = 0, ed = 0, small_bound = 0;
     p->meta_bytes = 0;
     for (uint64_t i = 0; i < nq; i++) {
         const rb_query &x = q[i];
@@ -1655,6 +1762,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
         else np = merge ? na : mn;
         d.n_slots = (uint32_t)ns;
         d.n_pos = (uint32_t)np;
+        small_bound += mn;   // matched keys: at most the smaller key count
         d.pos_base = npos;
         npos += np;
         ed += 2ull * (A->n_bitsets + B->n_bitsets) + ns / 16;
@@ -1682,6 +1790,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     p->total_pos = npos;
     p->total_tiles = tiles;
     p->defer_cap = std::max<uint64_t>(ed, 4096);
+    p->small_cap = small_bound + 2ull * SQCHUNK * lean_warps(p, current_schedule());
     if (use_bounds) {
         p->words_cap = bw;
         p->bits_cap = bb;
@@ -1719,6 +1828,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&p->ev2);
+    if (e == cudaSuccess) e = cudaEventCreate(&p->ev3);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -1774,6 +1884,14 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaEventRecordWithFlags(p->ev1, s, evf)) != cudaSuccess) return e;
     if (p->total_tiles) {
+        const unsigned grid = (unsigned)std::max<uint64_t>(
+            1, std::min<uint64_t>((p->small_cap + 31) / 32, (uint64_t)sm_count() * SMALL_CTAS_MAX * (LEAN_THREADS / 32)) /
+                   (LEAN_THREADS / 32));
+        k_small<<<grid, LEAN_THREADS, 0, s>>>(P);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaEventRecordWithFlags(p->ev3, s, evf)) != cudaSuccess) return e;
+    if (p->total_tiles) {
         switch (sc.warps_per_cta) {
             case 2: launch_heavy_w<2>(P, sc.ctas_per_sm, s); break;
             case 8: launch_heavy_w<8>(P, sc.ctas_per_sm, s); break;
@@ -1793,7 +1911,7 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
 }
 
 struct ArenaLayout {
-    uint64_t o_keys, o_defer, o_words, o_bits, bytes;
+    uint64_t o_keys, o_defer, o_small, o_words, o_bits, bytes;
     uint64_t words_cap;   // word region incl. the slack of k_lean's per-warp chunks
     uint64_t bits_cap;    // bitset region incl. the slack of k_heavy's per-warp chunks
 };
@@ -1803,7 +1921,8 @@ ArenaLayout arena_layout(const rb_plan *p) {
     const uint64_t T = p->total_pos;
     L.o_keys = align_up(8 * T, 256);
     L.o_defer = align_up(L.o_keys + 2 * T, 256);
-    L.o_words = align_up(L.o_defer + sizeof(Deferred) * p->defer_cap, 256);
+    L.o_small = align_up(L.o_defer + sizeof(Deferred) * p->defer_cap, 256);
+    L.o_words = align_up(L.o_small + sizeof(Item) * p->small_cap, 256);
     const rb_schedule sc = current_schedule();
     L.words_cap = p->words_cap + p->words_cap / 7 + (lean_warps(p, sc) + heavy_warps(p, sc)) * WCHUNK;
     L.o_bits = align_up(L.o_words + L.words_cap, 256);
@@ -1831,6 +1950,8 @@ rb_status run_launch(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena) {
     h.keys = (uint16_t *)((uint8_t *)a->ptr + L.o_keys);
     h.defer = (Deferred *)((uint8_t *)a->ptr + L.o_defer);
     h.defer_cap = p->defer_cap;
+    h.small = (Item *)((uint8_t *)a->ptr + L.o_small);
+    h.small_cap = p->small_cap;
     h.words_off = L.o_words;
     h.words_cap = L.words_cap;
     h.bits_off = L.o_bits;
@@ -1882,14 +2003,16 @@ rb_status run_wait(rb_plan *p, cudaStream_t s, bool graph, RbArena *a, RbArena *
         arena_unref(a);
         return cuda_err(e, "batch run");
     }
-    float m1 = 0.f, m2 = 0.f;
+    float m1 = 0.f, m2 = 0.f, m3 = 0.f;
     if (p->total_tiles && cudaEventElapsedTime(&m1, p->ev0, p->ev1) == cudaSuccess &&
-        cudaEventElapsedTime(&m2, p->ev1, p->ev2) == cudaSuccess) {
+        cudaEventElapsedTime(&m3, p->ev1, p->ev3) == cudaSuccess &&
+        cudaEventElapsedTime(&m2, p->ev3, p->ev2) == cudaSuccess) {
         p->last_lean_ms = m1;
+        p->last_small_ms = m3;
         p->last_heavy_ms = m2;
-        p->last_ms = m1 + m2;
+        p->last_ms = m1 + m3 + m2;
     } else {
-        p->last_ms = p->last_lean_ms = p->last_heavy_ms = 0;
+        p->last_ms = p->last_lean_ms = p->last_small_ms = p->last_heavy_ms = 0;
     }
     clear_stale_error();
     if (h.status & 4u) {
@@ -1901,6 +2024,7 @@ rb_status run_wait(rb_plan *p, cudaStream_t s, bool graph, RbArena *a, RbArena *
         p->words_cap = std::max<uint64_t>(p->words_cap, h.words_used);
         p->bits_cap = std::max<uint64_t>(p->bits_cap, h.bits_used);
         p->defer_cap = std::max<uint64_t>(p->defer_cap, h.defer_n);
+        p->small_cap = std::max<uint64_t>(p->small_cap, h.small_n1 + h.small_n2 + 2ull * SQCHUNK * lean_warps(p, current_schedule()));
         arena_unref(a);
         return RB_OK;
     }
@@ -1908,11 +2032,15 @@ rb_status run_wait(rb_plan *p, cudaStream_t s, bool graph, RbArena *a, RbArena *
         p->words_cap = h.words_used;
         p->bits_cap = h.bits_used;
         p->defer_cap = std::max<uint64_t>(h.defer_n, 1);
+        // later runs may reserve up to one block more per warp and class
+        p->small_cap = h.small_n1 + h.small_n2 + 2ull * SQCHUNK * lean_warps(p, current_schedule());
         p->exact = true;
     }
     p->last_lean_bytes = h.lean_bytes + p->meta_bytes;
+    p->last_small_bytes = h.small_bytes;
     p->last_heavy_bytes = h.heavy_bytes;
     p->last_deferred = h.defer_n;
+    p->last_small = h.small_n1 + h.small_n2;
     *arena = a;
     return RB_OK;
 }
@@ -1998,7 +2126,7 @@ rb_status finish_results(rb_plan *p, RbArena *a, rb_t **outs, uint64_t *counts) 
             outs[i] = h;
         }
     }
-    p->last_alg = alg + p->h_es->lean_bytes + p->meta_bytes + p->h_es->heavy_bytes;
+    p->last_alg = alg + p->h_es->lean_bytes + p->meta_bytes + p->h_es->small_bytes + p->h_es->heavy_bytes;
     p->last_out = outb;
     arena_unref(a);
     return RB_OK;
@@ -2153,6 +2281,9 @@ rb_status rb_plan_stats(const rb_plan_t *p, rb_plan_timing *t) {
     t->alg_bytes = p->last_alg;
     t->out_bytes = p->last_out;
     t->deferred = p->last_deferred;
+    t->small_ms = p->last_small_ms;
+    t->small_bytes = p->last_small_bytes;
+    t->small_pairs = p->last_small;
     return RB_OK;
 }
 
