@@ -69,20 +69,25 @@ def kernel_source_sha256():
     return h.hexdigest()
 
 
-def lean_traffic(alg_bytes):
-    """DRAM bytes of one materialising k_lean launch: the dram/algorithmic
-    byte ratio of the ncu capture summarised in profiles/ times this
-    launch's algorithmic bytes, or None when the kernel sources differ from
-    those the capture was taken from (or there is no capture)."""
-    import hashlib
+def kernel_traffic(kernel, alg_bytes):
+    """DRAM bytes of one launch of `kernel` in the materialising batch: the
+    dram/algorithmic byte ratio of its ncu capture summarised in profiles/
+    (a file named <kernel>_batched_*.md with "traffic_ratio:" and
+    "source_sha256:" lines) times this launch's algorithmic bytes, or None
+    when the kernel sources differ from those the capture was taken from (or
+    there is no capture)."""
+    import glob
     import re
-    try:
-        txt = open(os.path.join(ROOT, "profiles", "k_lean_batched_512pool_8192pairs.md")).read()
-        ratio = float(re.search(r"^traffic_ratio: ([0-9.]+)", txt, re.M).group(1))
-        want = re.search(r"^source_sha256: ([0-9a-f]{64})", txt, re.M).group(1)
-        return ratio * alg_bytes if kernel_source_sha256() == want else None
-    except Exception:
-        return None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_batched_*.md"))):
+        try:
+            txt = open(path).read()
+            ratio = float(re.search(r"^traffic_ratio: ([0-9.]+)", txt, re.M).group(1))
+            want = re.search(r"^source_sha256: ([0-9a-f]{64})", txt, re.M).group(1)
+        except Exception:
+            continue
+        if kernel_source_sha256() == want:
+            return ratio * alg_bytes
+    return None
 
 
 def dist_env():
@@ -425,26 +430,24 @@ def run_ours(args):
         return 0
 
     peak, peak_kind = measured_peaks()
-    lean_ms = statistics.mean(s["lean_ms"] for s in kms)
-    heavy_ms = statistics.mean(s["heavy_ms"] for s in kms)
-    lean_b = statistics.mean(s["lean_bytes"] for s in kms)
-    heavy_b = statistics.mean(s["heavy_bytes"] for s in kms)
-    if lean_ms >= heavy_ms:
-        dom, kernel_ms, alg_bytes = "k_lean (materialising batch)", lean_ms, lean_b
-    else:
-        dom, kernel_ms, alg_bytes = "k_heavy (materialising batch)", heavy_ms, heavy_b
+    mean = lambda xs, k: statistics.mean(x[k] for x in xs)
+    kern = {k: (mean(kms, k + "_ms"), mean(kms, k + "_bytes")) for k in ("lean", "small", "heavy")}
+    dom = max(kern, key=lambda k: kern[k][0])
+    kernel_ms, alg_bytes = kern[dom]
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    stage_gbs = (lean_b + heavy_b) / ((lean_ms + heavy_ms) / 1e3) / 1e9
+    stage_ms = sum(v[0] for v in kern.values())
+    stage_gbs = sum(v[1] for v in kern.values()) / (stage_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": args.traffic if args.traffic is not None else (
-                    lean_traffic(alg_bytes) if dom.startswith("k_lean") else None), "kernel": dom, "kernel_ms": kernel_ms,
+                "traffic": args.traffic if args.traffic is not None else kernel_traffic("k_" + dom, alg_bytes),
+                "kernel": f"k_{dom} (materialising batch)", "kernel_ms": kernel_ms,
                 "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
-                "pair_stage": {"lean_ms": lean_ms, "heavy_ms": heavy_ms, "lean_bytes": lean_b,
-                               "heavy_bytes": heavy_b, "achieved_gbs": stage_gbs, "frac": stage_gbs / peak,
-                               "deferred_pairs": statistics.mean(s["deferred"] for s in kms)},
-                "jaccard_stage": {"lean_ms": statistics.mean(s["lean_ms"] for s in jst),
-                                  "heavy_ms": statistics.mean(s["heavy_ms"] for s in jst),
-                                  "alg_bytes": statistics.mean(s["lean_bytes"] + s["heavy_bytes"] for s in jst)}}
+                "pair_stage": {**{f"{k}_ms": v[0] for k, v in kern.items()}, **{f"{k}_bytes": v[1] for k, v in kern.items()},
+                               "achieved_gbs": stage_gbs, "frac": stage_gbs / peak,
+                               "deferred_pairs": mean(kms, "deferred"), "small_pairs": mean(kms, "small_pairs")},
+                "jaccard_stage": {"lean_ms": mean(jst, "lean_ms"), "small_ms": mean(jst, "small_ms"),
+                                  "heavy_ms": mean(jst, "heavy_ms"),
+                                  "alg_bytes": statistics.mean(x["lean_bytes"] + x["small_bytes"] + x["heavy_bytes"]
+                                                               for x in jst)}}
 
     # per-pair baseline on the same GPU: rb_apply one pair at a time
     per = per_pair_leg(rb, G, ops, a, b, sizes, n=args.per_pair_sample)
@@ -461,8 +464,9 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}", "schedule": rb.get_schedule(),
                        "schedule_source": sched_info},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            # per step: k_lean + k_heavy + k_compact (materialising batch), k_lean + k_heavy (Jaccard batch)
-            "gpu_launches": 5 * args.steps,
+            # per step: k_lean + k_small + k_heavy + k_compact (materialising batch), k_lean + k_small +
+            # k_heavy (Jaccard batch)
+            "gpu_launches": 7 * args.steps,
             "clocks": clk,
             "step_ms_p50": statistics.median(step_ms), "step_ms_p99": float(np.percentile(step_ms, 99)),
             "per_pair": per, "bitset_and_or": bitset_legs, "configs": cfg_legs, "serving": serving}
@@ -512,9 +516,9 @@ def bitset_subset_legs(rb, G, pool, sizes, n_pairs=16384, reps=5):
                 stats.append(st)
         plan.free()
         hms = statistics.mean(s["heavy_ms"] for s in stats)
-        lms = statistics.mean(s["lean_ms"] for s in stats)
+        lms = statistics.mean(s["lean_ms"] + s["small_ms"] for s in stats)
         hb = statistics.mean(s["heavy_bytes"] for s in stats)
-        lb = statistics.mean(s["lean_bytes"] for s in stats)
+        lb = statistics.mean(s["lean_bytes"] + s["small_bytes"] for s in stats)
         units = float((sizes[a] + sizes[b]).sum())
         out[name] = {"pairs": int(len(a)), "gints_s": units / ((hms + lms) / 1e3) / 1e9,
                      "k_heavy": {"ms": hms, "alg_bytes": hb, "achieved_gbs": hb / hms / 1e6,
@@ -546,7 +550,7 @@ def tuned_schedule(rb, plan, args):
         e = cache[key]
         sc = e["schedule"]
         rb.set_schedule(sc["warps_per_cta"], sc["ctas_per_sm"], sc["small_intervals"], sc["lean_ctas_per_sm"],
-                        sc["prefetch_lines"])
+                        sc["prefetch_lines"], sc.get("tiles_per_take", 32))
         return {"source": f"schedule cache {path}", "tuned_ms": e.get("ms"), "tuned_at": e.get("at")}
     t0 = time.perf_counter()
     best, ms = plan.autotune(reps=1)
@@ -585,15 +589,14 @@ def plan_leg(rb, plan, units, steps=10, warmup=3):
         ms.append(e0.elapsed_time(e1))
         st.append(plan.stats())
     t = statistics.median(ms)
-    lm = statistics.mean(x["lean_ms"] for x in st)
-    hm = statistics.mean(x["heavy_ms"] for x in st)
-    lb = statistics.mean(x["lean_bytes"] for x in st)
-    hb = statistics.mean(x["heavy_bytes"] for x in st)
-    kern, kms, kb = ("k_lean", lm, lb) if lm >= hm else ("k_heavy", hm, hb)
+    ks = {k: (statistics.mean(x[k + "_ms"] for x in st), statistics.mean(x[k + "_bytes"] for x in st))
+          for k in ("lean", "small", "heavy")}
+    kern = max(ks, key=lambda k: ks[k][0])
+    kms, kb = ks[kern]
     gbs = kb / (kms / 1e3) / 1e9 if kms > 0 else 0.0
     return {"ms": t, "gints_s": units / (t / 1e3) / 1e9,
-            "roofline": {"kernel": kern, "kernel_ms": kms, "alg_bytes": kb, "achieved_gbs": gbs, "frac": gbs / peak,
-                         "lean_ms": lm, "heavy_ms": hm}}
+            "roofline": {"kernel": "k_" + kern, "kernel_ms": kms, "alg_bytes": kb, "achieved_gbs": gbs,
+                         "frac": gbs / peak, **{f"{k}_ms": v[0] for k, v in ks.items()}}}
 
 
 def config_legs(rb, args, budget_s=4.0):

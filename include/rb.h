@@ -241,18 +241,22 @@ void rb_plan_free(rb_plan_t *p);
 
 /* Launch schedule of the container-pair kernels: the heavy kernel's warps
  * per CTA (2, 4 or 8; each warp owns 16 KB of shared tiles) and CTAs per SM;
- * the largest array pair (values on both sides) that one lane of the lean
- * kernel merges alone (larger array pairs up to 1024 values are merged by the
- * whole warp; bitsets and larger containers are deferred to the heavy
- * kernel); the lean kernel's CTAs of 128 threads per SM (0 = 8, the most that fit); and how many
- * 128-byte lines of each queued container's payload the lean kernel hints
- * into L2 ahead of use (0 = none). */
+ * the largest array pair (values on both sides) that one lane of the
+ * small-pair kernel merges alone (larger array pairs up to 254 values are
+ * merged by groups of 8 lanes, up to 1022 by the whole warp; bitsets and
+ * larger containers are deferred to the heavy kernel); the lean kernel's
+ * CTAs of 128 threads per SM (0 = 8, the most that fit); how many 128-byte
+ * lines of each queued container's payload the lean kernel hints into L2
+ * ahead of use (0 = none); and how many consecutive 32-slot tiles a lean
+ * kernel warp takes from the shared work counter at once (1 .. 256; 0 =
+ * 32). */
 typedef struct {
     uint32_t warps_per_cta;
     uint32_t ctas_per_sm;
     uint32_t small_intervals;
     uint32_t lean_ctas_per_sm;
     uint32_t prefetch_lines;
+    uint32_t tiles_per_take;
 } rb_schedule;
 rb_status rb_set_schedule(const rb_schedule *s);
 rb_status rb_get_schedule(rb_schedule *s);
@@ -260,7 +264,8 @@ rb_status rb_get_schedule(rb_schedule *s);
 /* Tune the schedule on the plan (no paper counterpart): coordinate descent
  * from the current schedule over the heavy kernel's shape ({2,6}, {4,3},
  * {8,1} warps per CTA x CTAs per SM), small_intervals (32, 48, 64, 96, 128),
- * lean_ctas_per_sm (6, 7, 8) and prefetch_lines (0, 2, 4, 8): each pass
+ * lean_ctas_per_sm (6, 7, 8), prefetch_lines (0, 2, 4, 8) and
+ * tiles_per_take (8, 16, 32, 64): each pass
  * times every value of one knob with the others fixed (one warm-up run,
  * then reps runs, CUDA events on `stream`, key merge + container-pair
  * kernels) and keeps the fastest, until a pass changes nothing (at most 3

@@ -38,12 +38,12 @@ class Query(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("small_intervals", ctypes.c_uint32), ("lean_ctas_per_sm", ctypes.c_uint32),
-                ("prefetch_lines", ctypes.c_uint32)]
+                ("prefetch_lines", ctypes.c_uint32), ("tiles_per_take", ctypes.c_uint32)]
 
     def as_dict(self):
         return {"warps_per_cta": self.warps_per_cta, "ctas_per_sm": self.ctas_per_sm,
                 "small_intervals": self.small_intervals, "lean_ctas_per_sm": self.lean_ctas_per_sm,
-                "prefetch_lines": self.prefetch_lines}
+                "prefetch_lines": self.prefetch_lines, "tiles_per_take": self.tiles_per_take}
 
 
 class PlanTiming(ctypes.Structure):
@@ -515,8 +515,8 @@ def get_schedule() -> dict:
 
 
 def set_schedule(warps_per_cta: int, ctas_per_sm: int, small_intervals: int, lean_ctas_per_sm: int = 0,
-                 prefetch_lines: int = 4):
-    s = Schedule(warps_per_cta, ctas_per_sm, small_intervals, lean_ctas_per_sm, prefetch_lines)
+                 prefetch_lines: int = 0, tiles_per_take: int = 32):
+    s = Schedule(warps_per_cta, ctas_per_sm, small_intervals, lean_ctas_per_sm, prefetch_lines, tiles_per_take)
     _check(lib().rb_set_schedule(ctypes.byref(s)))
 
 

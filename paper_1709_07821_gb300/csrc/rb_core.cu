@@ -19,7 +19,7 @@ std::mutex g_alloc_mu;
 rb_alloc_fn g_alloc = nullptr;
 rb_free_fn g_free = nullptr;
 void *g_alloc_ctx = nullptr;
-rb_schedule g_sched = {4, 3, 64, 0, 4};
+rb_schedule g_sched = {4, 3, 96, 0, 0, 32};
 std::mutex g_sched_mu;
 }  // namespace
 
@@ -483,6 +483,7 @@ rb_status rb_set_schedule(const rb_schedule *s) {
     if (s->small_intervals > 2047) return set_err(RB_EINVAL, "small_intervals must be <= 2047");
     if (s->lean_ctas_per_sm > 8) return set_err(RB_EINVAL, "lean_ctas_per_sm must be <= 8");
     if (s->prefetch_lines > 64) return set_err(RB_EINVAL, "prefetch_lines must be <= 64");
+    if (s->tiles_per_take > 256) return set_err(RB_EINVAL, "tiles_per_take must be <= 256");
     std::lock_guard<std::mutex> g(g_sched_mu);
     g_sched = *s;
     return RB_OK;

@@ -1666,7 +1666,7 @@ struct rb_plan {
     bool pending_graph = false;
     cudaStream_t pending_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
-    rb_schedule gsched = {0, 0, 0, 0, 0};
+    rb_schedule gsched = {0, 0, 0, 0, 0, 0};
     double last_ms = 0, last_lean_ms = 0, last_small_ms = 0, last_heavy_ms = 0;
     uint64_t last_alg = 0, last_out = 0, last_lean_bytes = 0, last_small_bytes = 0, last_heavy_bytes = 0;
     uint64_t last_deferred = 0, last_small = 0;
@@ -1874,7 +1874,7 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     P.n_pairs = (uint32_t)nq;
     P.small_iv = sc.small_intervals;
     P.prefetch = sc.prefetch_lines;
-    P.chunk = 4;
+    P.chunk = sc.tiles_per_take ? sc.tiles_per_take : 32;
     init_kernel_attrs();
     if ((e = cudaEventRecordWithFlags(p->ev0, s, evf)) != cudaSuccess) return e;
     if (p->total_tiles) {
@@ -2313,16 +2313,18 @@ rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *be
     // Coordinate descent from the current schedule over the knobs that
     // change the kernels' speed: the heavy kernel's shape (warps per CTA x
     // CTAs per SM), the largest array pair one lane merges alone (larger
-    // ones go to 8-lane groups), the lean kernel's CTAs per SM and the L2
-    // prefetch depth.  Each pass tries every value of one knob with the
+    // ones go to 8-lane groups), the lean kernel's CTAs per SM, the L2
+    // prefetch depth and the tiles a lean warp takes at once.  Each pass tries every value of one knob with the
     // others fixed and keeps the fastest; it stops after a pass that
     // changes nothing (at most three passes).
     static const uint32_t heavy[][2] = {{2, 6}, {4, 3}, {8, 1}};
     static const uint32_t smalls[] = {32, 48, 64, 96, 128};
     static const uint32_t leans[] = {6, 7, LEAN_CTAS_MAX};
     static const uint32_t prefs[] = {0, 2, 4, 8};
+    static const uint32_t takes[] = {8, 16, 32, 64};
     rb_schedule win = saved;
     if (win.lean_ctas_per_sm == 0) win.lean_ctas_per_sm = LEAN_CTAS_MAX;
+    if (win.tiles_per_take == 0) win.tiles_per_take = 32;
     double win_ms = measure(win);
     if (win_ms < 0) win_ms = 1e30;
     auto consider = [&](const rb_schedule &c) -> bool {
@@ -2356,6 +2358,11 @@ rb_status rb_autotune(rb_plan_t *p, uint32_t reps, void *stream, rb_schedule *be
         for (uint32_t v : prefs) {
             rb_schedule c = win;
             c.prefetch_lines = v;
+            changed |= consider(c);
+        }
+        for (uint32_t v : takes) {
+            rb_schedule c = win;
+            c.tiles_per_take = v;
             changed |= consider(c);
         }
         if (!changed) break;

@@ -158,7 +158,8 @@ def test_schedules_agree(rb, orc):
             for op in OPS:
                 assert_layout_eq(A.op(op, B).layout(), OA.op(op, OB).layout(), f"sched {w},{c},{s} op{op}")
     finally:
-        rb.set_schedule(saved["warps_per_cta"], saved["ctas_per_sm"], saved["small_intervals"])
+        rb.set_schedule(saved["warps_per_cta"], saved["ctas_per_sm"], saved["small_intervals"],
+                        saved["lean_ctas_per_sm"], saved["prefetch_lines"], saved["tiles_per_take"])
 
 
 def _pool(workloads_mod, name, n, hi, seed=None):
@@ -424,7 +425,7 @@ def test_autotune_then_results_match_the_oracle(rb, orc, workloads_mod):
         best, ms = plan.autotune(reps=1)
         assert ms > 0 and rb.get_schedule() == best
         assert best["small_intervals"] in (32, 48, 64, 96, 128) and best["lean_ctas_per_sm"] in (6, 7, 8)
-        assert best["prefetch_lines"] in (0, 2, 4, 8)
+        assert best["prefetch_lines"] in (0, 2, 4, 8) and best["tiles_per_take"] in (8, 16, 32, 64)
         outs, counts = plan.run()
         for i in range(len(ops)):
             exp = O[a[i]].op(int(ops[i]), O[b[i]])
@@ -432,5 +433,5 @@ def test_autotune_then_results_match_the_oracle(rb, orc, workloads_mod):
             assert_layout_eq(outs[i].layout(), exp.layout(), f"tuned pair {i}")
     finally:
         rb.set_schedule(saved["warps_per_cta"], saved["ctas_per_sm"], saved["small_intervals"],
-                        saved["lean_ctas_per_sm"], saved["prefetch_lines"])
+                        saved["lean_ctas_per_sm"], saved["prefetch_lines"], saved["tiles_per_take"])
         plan.free()
