@@ -249,7 +249,8 @@ void rb_plan_free(rb_plan_t *p);
  * lines of each queued container's payload the lean kernel hints into L2
  * ahead of use (0 = none); and how many consecutive 32-slot tiles a lean
  * kernel warp takes from the shared work counter at once (1 .. 256; 0 =
- * 32). */
+ * 32; plans too small to give every warp about 64 takes of that size take
+ * fewer). */
 typedef struct {
     uint32_t warps_per_cta;
     uint32_t ctas_per_sm;

@@ -1874,7 +1874,14 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     P.n_pairs = (uint32_t)nq;
     P.small_iv = sc.small_intervals;
     P.prefetch = sc.prefetch_lines;
-    P.chunk = sc.tiles_per_take ? sc.tiles_per_take : 32;
+    // consecutive tiles per take: the schedule's, fewer for small plans so
+    // that every lean warp still gets some 64 takes (the last takes of a
+    // run are what balances its warps)
+    {
+        const uint64_t take = sc.tiles_per_take ? sc.tiles_per_take : 32;
+        const uint64_t fair = p->total_tiles / (lean_warps(p, sc) * 64);
+        P.chunk = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(take, fair));
+    }
     init_kernel_attrs();
     if ((e = cudaEventRecordWithFlags(p->ev0, s, evf)) != cudaSuccess) return e;
     if (p->total_tiles) {
