@@ -348,6 +348,12 @@ def run_ours(args):
     pool_bytes = sum(g.payload_bytes() + 10 * g.n_containers for g in G)
     log(f"rank {rank}: built {len(G)} device bitmaps ({pool_bytes / 1e9:.2f} GB) in {time.time() - t0:.1f}s")
 
+    if args.subsets_only:
+        # the bitset-dominated legs alone (profiling k_heavy)
+        names = tuple(args.subset.split(",")) if args.subset else None
+        print(json.dumps({"bitset_and_or": bitset_subset_legs(rb, G, pool, sizes, only=names)}))
+        return 0
+
     if args.serving_only:
         # the serving leg alone (profiling the multi-way kernels)
         rates = tuple(float(x) for x in args.serving_rates.split(","))
@@ -476,7 +482,7 @@ def run_ours(args):
     return 0
 
 
-def bitset_subset_legs(rb, G, pool, sizes, n_pairs=16384, reps=5):
+def bitset_subset_legs(rb, G, pool, sizes, n_pairs=16384, reps=5, only=None):
     """Bitset-dominated AND/OR: pairs of dense-clustered pool bitmaps (ops AND
     and OR, 50/50), (1) drawn uniformly, (2) drawn among pairs whose key
     ranges overlap, so that bitset x bitset pairs are actually combined."""
@@ -501,6 +507,8 @@ def bitset_subset_legs(rb, G, pool, sizes, n_pairs=16384, reps=5):
         pick = over[rng.choice(len(over), n_pairs)]
         sets["overlapping"] = (pick[:, 0], pick[:, 1])
     for name, (a, b) in sets.items():
+        if only and name not in only:
+            continue
         keep = a != b
         a, b = a[keep].astype(np.uint32), b[keep].astype(np.uint32)
         ops = rng.integers(0, 2, len(a)).astype(np.uint32)
@@ -877,6 +885,8 @@ def main():
     ap.add_argument("--log10-hi", type=float, default=0.0, help="scaled case: top of the cardinality law")
     ap.add_argument("--schedule", default="", help="warps_per_cta,ctas_per_sm,small_intervals")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving leg (profiling)")
+    ap.add_argument("--subsets-only", action="store_true", help="run only the bitset-dominated legs (profiling)")
+    ap.add_argument("--subset", default="", help="with --subsets-only: uniform, overlapping or both (comma list)")
     ap.add_argument("--serving-rates", default="1e3,1e4,1e5,1e6", help="offered loads of the serving-only run")
     ap.add_argument("--serving-queries", type=int, default=40000, help="queries per load, serving-only run")
     ap.add_argument("--traffic", type=float, default=None,
