@@ -410,7 +410,7 @@ __device__ __forceinline__ uint32_t array_result_bound(uint32_t op, uint32_t na,
 // lanes' word offsets.  The words move 128 per round, 4 loads per lane in
 // flight; the first round is read before the allocation returns.  Writes
 // the results and adds them to the query's sums.
-__device__ __noinline__ void copy_tile(ExecState *es, unsigned long long *wa, unsigned long long pos_base, bool mine,
+__device__ __forceinline__ void copy_tile(ExecState *es, unsigned long long *wa, unsigned long long pos_base, bool mine,
                                        uint64_t dx, const uint8_t *base, uint32_t key, uint32_t pos,
                                        unsigned long long &acc, uint32_t lane) {
     const uint32_t ty = d_type(dx), c = d_card(dx), r = ty == T_RUN ? d_runs(dx) : 0;
@@ -590,7 +590,7 @@ __device__ __forceinline__ unsigned long long sq_take(unsigned long long *ctr, u
 
 // append the tile's small container pairs (lanes in am) to the small-pair
 // queue: one-lane items (one1) from the bottom, the others from the top
-__device__ __noinline__ void queue_small(ExecState *es, unsigned long long *qs, uint32_t am, bool mine, bool one1,
+__device__ __forceinline__ void queue_small(ExecState *es, unsigned long long *qs, uint32_t am, bool mine, bool one1,
                                          uint64_t da, uint64_t db, uint32_t p, uint32_t pos, uint32_t info,
                                          uint32_t lane) {
     const uint32_t m1 = __ballot_sync(FULL, mine && one1), m2 = am & ~m1;
