@@ -321,9 +321,13 @@ void rb_accum_free(rb_accum_t *acc);
  * max_batch per batch), and launches each batch on its own stream, so
  * batches overlap on the device while new requests keep arriving
  * (continuous batching).  Result memory is charged to mem_budget until the
- * caller frees the result; the loop allocates it with cudaMallocAsync from
- * its own thread.  rb_server_destroy completes batches in flight and fails
- * requests never admitted with RB_EBUSY. */
+ * caller frees the result; the loop allocates it (and each batch's tables)
+ * with cudaMallocAsync from its own thread, not through the installed
+ * allocator, whose hooks may have to run on the caller's thread (a Python
+ * allocator needs the interpreter lock).  The index table is allocated by
+ * rb_server_create through the installed allocator.  rb_server_destroy
+ * completes batches in flight and fails requests never admitted with
+ * RB_EBUSY. */
 #define RB_SERVE_MAX_K 8
 typedef struct {
     uint32_t op;            /* RB_AND or RB_OR */

@@ -264,15 +264,24 @@ rb_status rb_server_create(const rb_t *const *index, uint32_t n, uint64_t mem_bu
         if (!index[i]) { budget_unref(S->budget); delete S; return set_err(RB_EINVAL, "index[%u] is NULL", i); }
         hv[i] = view_of(index[i]);
     }
-    cudaError_t e = cudaMalloc((void **)&S->d_index, sizeof(BmView) * std::max<uint32_t>(n, 1));
-    if (e == cudaSuccess && n) e = cudaMemcpy(S->d_index, hv.data(), sizeof(BmView) * n, cudaMemcpyHostToDevice);
+    // the index table comes from the installed allocator, on the calling
+    // thread (the legacy default stream; the copy below completes before the
+    // loop starts)
+    S->d_index = (BmView *)dev_alloc(sizeof(BmView) * std::max<uint32_t>(n, 1), nullptr);
+    if (!S->d_index) {
+        budget_unref(S->budget);
+        delete S;
+        return RB_ENOMEM;
+    }
+    cudaError_t e = cudaSuccess;
+    if (n) e = cudaMemcpy(S->d_index, hv.data(), sizeof(BmView) * n, cudaMemcpyHostToDevice);
     S->slots.resize(max_inflight_batches);
     for (auto &sl : S->slots)
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.s, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         for (auto &sl : S->slots)
             if (sl.s) cudaStreamDestroy(sl.s);
-        if (S->d_index) cudaFree(S->d_index);
+        dev_free(S->d_index, sizeof(BmView) * std::max<uint32_t>(n, 1), nullptr);
         budget_unref(S->budget);
         delete S;
         return cuda_err(e, "rb_server_create");
@@ -422,7 +431,7 @@ void rb_server_destroy(rb_server_t *S) {
         }
         if (sl.stage.p) cudaFreeHost(sl.stage.p);
     }
-    if (S->d_index) cudaFree(S->d_index);
+    dev_free(S->d_index, sizeof(BmView) * std::max<uint32_t>(S->n, 1), nullptr);
     {
         // results that outlive the loop stop waking it before it is deleted
         std::lock_guard<std::mutex> g(S->budget->mu);
