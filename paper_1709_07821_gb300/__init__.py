@@ -171,8 +171,10 @@ def _check(st):
 
 
 def _stream(stream=None):
+    """A cudaStream_t: stream (a torch.cuda.Stream or a raw handle), else
+    PyTorch's current stream."""
     if stream is not None:
-        return ctypes.c_void_p(int(stream))
+        return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
