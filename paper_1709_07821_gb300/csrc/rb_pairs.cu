@@ -427,7 +427,6 @@ __device__ __forceinline__ void copy_tile(ExecState *es, unsigned long long *wa,
     // word g of the tile's copies: its container is the lane j whose words
     // [wincl_j - nw_j, wincl_j) hold g, found by a 5-step search over lanes
     auto gather = [&](uint32_t g) -> uint32_t {
-        if (one) return g < T ? __ldg(S1 + g) : 0u;
         uint32_t j = 0;
 #pragma unroll
         for (uint32_t s = 16; s; s >>= 1)
@@ -436,32 +435,48 @@ __device__ __forceinline__ void copy_tile(ExecState *es, unsigned long long *wa,
         const uint32_t ex = __shfl_sync(FULL, wincl - nw, j);
         return g < T ? __ldg(S + (g - ex)) : 0u;
     };
-    // the first round is read before the allocation returns; one contiguous
-    // source moves 256 words per round (8 loads per lane in flight), a
-    // gathered one 128 (4 loads, each after its container search)
+    // The first round is read before the allocation returns.  A contiguous
+    // source is copied to a destination placed at the same address modulo
+    // 16 (the allocation takes 12 bytes more), so that its 16-byte-aligned
+    // body moves as 16-byte vectors, 512 words per round (4 per lane in
+    // flight), and at most 3 words at each end move alone; a gathered source
+    // moves 128 words per round (4 loads, each after its container search).
     unsigned long long wbase = 0;
+    uint32_t shift = 0;
     bool ok = true;
     uint32_t *D = nullptr;
     if (one) {
-        for (uint32_t g0 = 0;; g0 += 32 * 8) {
-            uint32_t v[8];
+        const uint64_t s0 = reinterpret_cast<uint64_t>(S1);
+        const uint32_t hw = min((uint32_t)(((16u - (uint32_t)(s0 & 15u)) & 15u) >> 2), T);   // head words
+        const uint32_t nv = (T - hw) >> 2, tw = T - hw - 4 * nv;                            // body vectors, tail words
+        const uint4 *SV = reinterpret_cast<const uint4 *>(S1 + hw);
+        const bool has_h = lane < hw, has_t = lane >= 4 && lane < 4 + tw;
+        const uint32_t hv = has_h ? __ldg(S1 + lane) : 0u;
+        const uint32_t tv = has_t ? __ldg(S1 + hw + 4 * nv + (lane - 4)) : 0u;
+        for (uint32_t v0 = 0;; v0 += 32 * 4) {
+            uint4 x[4];
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const uint32_t g = g0 + 32u * k + lane;
-                v[k] = g < T ? __ldg(S1 + g) : 0u;
+            for (int k = 0; k < 4; k++) {
+                const uint32_t vi = v0 + 32u * k + lane;
+                x[k] = vi < nv ? __ldg(SV + vi) : make_uint4(0u, 0u, 0u, 0u);
             }
-            if (g0 == 0) {
-                wbase = lean_alloc(es, wa, total, lane);
+            if (v0 == 0) {
+                wbase = lean_alloc(es, wa, total + 12, lane);
                 ok = wbase != ALLOC_FAIL;
                 if (!ok) break;
-                D = reinterpret_cast<uint32_t *>(es->arena + es->words_off + wbase);
+                const uint64_t d0 = reinterpret_cast<uint64_t>(es->arena + es->words_off + wbase);
+                shift = (uint32_t)((s0 - d0) & 15u);
+                D = reinterpret_cast<uint32_t *>(d0 + shift);
+                if (has_h) D[lane] = hv;
+                if (has_t) D[hw + 4 * nv + (lane - 4)] = tv;
             }
+            uint4 *DV = reinterpret_cast<uint4 *>(D + hw);
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const uint32_t g = g0 + 32u * k + lane;
-                if (g < T) D[g] = v[k];
+            for (int k = 0; k < 4; k++) {
+                const uint32_t vi = v0 + 32u * k + lane;
+                if (vi < nv) DV[vi] = x[k];
             }
-            if (g0 + 32 * 8 >= T) break;
+            if (v0 + 32 * 4 >= nv) break;
         }
     } else
     for (uint32_t g0 = 0;; g0 += 128) {
@@ -480,7 +495,7 @@ __device__ __forceinline__ void copy_tile(ExecState *es, unsigned long long *wa,
         if (g0 + 128 >= T) break;
     }
     if (mine) {
-        es->descs[pos_base + pos] = ok ? mk_desc(c, ty, r, es->words_off + wbase + incl - bytes) : DESC_EMPTY;
+        es->descs[pos_base + pos] = ok ? mk_desc(c, ty, r, es->words_off + wbase + shift + incl - bytes) : DESC_EMPTY;
         es->keys[pos_base + pos] = (uint16_t)key;
         acc += in_payload_bytes(dx) + (ok ? payload_bytes(ty, c, r) + META_BYTES : 0);
     }
