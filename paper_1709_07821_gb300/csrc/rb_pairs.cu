@@ -344,36 +344,37 @@ __device__ __forceinline__ uint32_t keep_table(uint32_t op) {
 }
 
 // one lane merges two small sorted arrays without branches on the data: each
-// step takes the smaller head (a first on a tie), notes whether the other
-// input holds it, and keeps it by the op's table; counts cardinality c and
-// runs r, and with EMIT writes the kept values.  a and b are generic
-// pointers: the arrays staged in shared memory, or in global memory.
+// step compares the two heads, keeps the smaller one (either one when they
+// are equal, and then both advance) by the op's table, and advances the
+// input(s) it came from; counts cardinality c and runs r, and with EMIT
+// writes the kept values.  a and b are generic pointers: the arrays staged
+// in shared memory, or in global memory.
 template <bool EMIT>
 __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *a, uint32_t na, const uint16_t *b,
                                                   uint32_t nb, uint32_t &c, uint32_t &r, uint16_t *out) {
-    uint32_t i = 0, j = 0, pa = 0xFFFFFFFFu, last = 0xFFFFFFFEu;
+    // what the table keeps: a value only a holds (bit 2), only b holds
+    // (bit 0), both hold (bit 3, taken from a)
+    const bool k_a = (tbl & 4u) != 0, k_b = (tbl & 1u) != 0, k_ab = (tbl & 8u) != 0;
+    uint32_t i = 0, j = 0, last = 0xFFFFFFFEu;
     c = 0;
     r = 0;
     // once one input is exhausted the rest of the other is kept whole or
     // dropped whole: AND stops at the first end, ANDNOT once a ends, OR and
     // XOR run to both ends
-    const bool keep_a_rest = (tbl & 4u) != 0, keep_b_rest = (tbl & 1u) != 0;
 #pragma unroll 1
-    while ((i < na && (j < nb || keep_a_rest)) || (j < nb && keep_b_rest)) {
+    while ((i < na && (j < nb || k_a)) || (j < nb && k_b)) {
         const uint32_t va = i < na ? (uint32_t)a[i] : KEY_END;
         const uint32_t vb = j < nb ? (uint32_t)b[j] : KEY_END;
-        const bool ta = va <= vb;
-        const uint32_t v = ta ? va : vb;
-        const bool ino = ta ? (vb == va) : (pa == vb);
-        if ((tbl >> ((ta ? 2u : 0u) | (ino ? 1u : 0u))) & 1u) {
+        const bool lt = va < vb, gt = vb < va;
+        const uint32_t v = gt ? vb : va;
+        if (lt ? k_a : gt ? k_b : k_ab) {
             if (EMIT) out[c] = (uint16_t)v;
             r += (v != last + 1);
             last = v;
             c++;
         }
-        pa = ta ? va : pa;
-        i += ta;
-        j += !ta;
+        i += !gt;
+        j += !lt;
     }
 }
 
