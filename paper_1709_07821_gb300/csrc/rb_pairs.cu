@@ -93,6 +93,7 @@ struct ExecState {
     unsigned long long defer_cap, defer_n;
     unsigned long long small_cap, small_n1, small_n2, swork1, swork2;
     unsigned long long lean_bytes, heavy_bytes, small_bytes;
+    unsigned long long cwork;   // k_compact's query counter
     unsigned int status, pad;
 };
 
@@ -1599,14 +1600,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_heavy(PairParams P) {
 
 // drop empty results: in-place stream compaction of each query's output
 // range (positions are already in key order), one block per query
-__global__ void __launch_bounds__(512) k_compact(const PairDev *pairs, uint32_t n_pairs, PairStats *stats,
-                                                 const ExecState *es) {
+// blocks take queries from a shared counter in the order `order` gives
+// (materialising queries by decreasing number of positions, so that the
+// largest are not left for the end)
+__global__ void __launch_bounds__(512) k_compact(const PairDev *pairs, const uint32_t *order, uint32_t n_order,
+                                                 PairStats *stats, ExecState *es) {
     __shared__ uint32_t s_w[16];
-    __shared__ uint32_t s_tot;
+    __shared__ uint32_t s_tot, s_next;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (uint32_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
+    for (;;) {
+        if (tid == 0) s_next = (uint32_t)atomicAdd(&es->cwork, 1ull);
+        __syncthreads();
+        const uint32_t x = s_next;
+        __syncthreads();
+        if (x >= n_order) break;
+        const uint32_t p = order[x];
         const PairDev pd = pairs[p];
-        if (pd.flags & F_COUNT) continue;
         const uint32_t n = pd.n_pos;
         uint64_t *D = es->descs + pd.pos_base;
         uint16_t *K = es->keys + pd.pos_base;
@@ -1674,6 +1683,8 @@ struct rb_plan {
     unsigned long long *d_tile_base = nullptr;
     PairStats *d_stats = nullptr;
     ExecState *d_es = nullptr;
+    uint32_t *d_order = nullptr;   // materialising queries by decreasing positions (k_compact)
+    uint32_t n_order = 0;
     PairStats *h_stats = nullptr;
     ExecState *h_es = nullptr;
     cudaStream_t ps = nullptr;
@@ -1819,7 +1830,8 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     const uint64_t o_pairs = align_up(o_pool + sizeof(BmView) * (uint64_t)pool_n, 256);
     const uint64_t o_qv = align_up(o_pairs + sizeof(PairDev) * nq, 256);
     const uint64_t o_tb = align_up(o_qv + sizeof(QViews) * nq, 256);
-    const uint64_t o_stats = align_up(o_tb + 8ull * (nq + 1), 256);
+    const uint64_t o_ord = align_up(o_tb + 8ull * (nq + 1), 256);
+    const uint64_t o_stats = align_up(o_ord + 4ull * std::max<uint64_t>(nq, 1), 256);
     const uint64_t o_es = align_up(o_stats + sizeof(PairStats) * nq, 256);
     p->tables_bytes = o_es + 256;
     p->tables = (uint8_t *)dev_alloc(p->tables_bytes, s);
@@ -1828,6 +1840,7 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     p->d_pairs = (PairDev *)(p->tables + o_pairs);
     p->d_qv = (QViews *)(p->tables + o_qv);
     p->d_tile_base = (unsigned long long *)(p->tables + o_tb);
+    p->d_order = (uint32_t *)(p->tables + o_ord);
     p->d_stats = (PairStats *)(p->tables + o_stats);
     p->d_es = (ExecState *)(p->tables + o_es);
     std::vector<uint8_t> hbuf(o_stats);
@@ -1837,6 +1850,16 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     QViews *hq = (QViews *)(hbuf.data() + o_qv);
     for (uint64_t i = 0; i < nq; i++) hq[i] = {hv[p->pairs[i].a], hv[p->pairs[i].b]};
     memcpy(hbuf.data() + o_tb, tb.data(), 8ull * (nq + 1));
+    {
+        std::vector<uint32_t> ord;
+        ord.reserve(nq);
+        for (uint64_t i = 0; i < nq; i++)
+            if (!(p->pairs[i].flags & F_COUNT) && p->pairs[i].n_pos) ord.push_back((uint32_t)i);
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](uint32_t x, uint32_t y) { return p->pairs[x].n_pos > p->pairs[y].n_pos; });
+        p->n_order = (uint32_t)ord.size();
+        if (!ord.empty()) memcpy(hbuf.data() + o_ord, ord.data(), 4ull * ord.size());
+    }
     cudaError_t e = cudaMallocHost((void **)&p->h_stats, sizeof(PairStats) * std::max<uint64_t>(nq, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&p->h_es, sizeof(ExecState));
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->tables, hbuf.data(), o_stats, cudaMemcpyHostToDevice, s);
@@ -1923,9 +1946,9 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = cudaEventRecordWithFlags(p->ev2, s, evf)) != cudaSuccess) return e;
-    if (p->any_mat) {
-        unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(nq, (uint64_t)sm_count() * 8));
-        k_compact<<<grid, 512, 0, s>>>(p->d_pairs, (uint32_t)nq, p->d_stats, p->d_es);
+    if (p->any_mat && p->n_order) {
+        unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(p->n_order, (uint64_t)sm_count() * 4));
+        k_compact<<<grid, 512, 0, s>>>(p->d_pairs, p->d_order, p->n_order, p->d_stats, p->d_es);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (nq) e = cudaMemcpyAsync(p->h_stats, p->d_stats, sizeof(PairStats) * nq, cudaMemcpyDeviceToHost, s);
