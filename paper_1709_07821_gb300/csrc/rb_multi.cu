@@ -113,12 +113,14 @@ __device__ uint64_t alloc_b(MState *es, uint32_t lane) {
 // member for the key range the tile spans, then a coalesced scan of that
 // range (or, when a member holds many more keys there, a binary search per
 // output key).  A key whose containers are all arrays with at most LCAP
-// values in play is then merged by its own lane (OR: successive merges of
-// the sorted arrays; AND: the smallest array filtered by binary search in
-// the others), in lane-private columns of the two tiles; the other keys are
-// folded by the whole warp in the tiles, as the general path does.
+// values in play is then merged by its own lane (OR: one k-way merge of the
+// sorted arrays; AND: the smallest array filtered by binary search in the
+// others) from its arrays staged in the lane's slice of the warp's tiles,
+// straight into its output; the other keys are folded by the whole warp in
+// the tiles, as the general path does.
 constexpr uint32_t MK = 8;
-constexpr uint32_t LCAP = 256;   // both tiles as 8192 u16 / 32 lanes
+constexpr uint32_t LCAP = 256;   // values in play that one lane merges alone (the rest: the warp, in tiles)
+constexpr uint32_t LSLICE_WORDS = 128;   // a lane's staging slice of the warp's two tiles (32 x 512 B = 16 KB)
 constexpr uint32_t NOIX = 0xFFFFFFFFu;
 constexpr uint32_t MKEY_END = 0x10000u;
 
@@ -149,10 +151,16 @@ __device__ __forceinline__ uint32_t nth_set_bit(uint64_t x, uint32_t n) {
     return b;
 }
 
-// element e of a lane's column in the warp's two tiles used as 8192 u16
-// (conflict-light: consecutive lanes share 4-byte words)
-__device__ __forceinline__ uint16_t &col(uint64_t *T, uint32_t e, uint32_t lane) {
-    return reinterpret_cast<uint16_t *>(T)[e * 32 + lane];
+// first index in sorted a[0..n) (shared or global memory) holding a value >= v
+__device__ __forceinline__ uint32_t lower_bound_gen(const uint16_t *a, uint32_t n, uint32_t v) {
+    uint32_t lo = 0, hi = n;
+#pragma unroll 1
+    while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if ((uint32_t)a[m] < v) lo = m + 1;
+        else hi = m;
+    }
+    return lo;
 }
 
 // first index in sorted a[0..n) holding a value >= v
@@ -176,40 +184,6 @@ __device__ __forceinline__ uint32_t lb_from(const uint16_t *keys, uint32_t n, ui
     const uint32_t r = lower_bound16(keys + start, w, key);
     if (r < w || start + w == n) return start + r;
     return start + w + lower_bound16(keys + start + w, n - start - w, key);
-}
-
-// count c, runs r and canonical encoding of a lane's column X[0..n); writes
-// the container at out (4-byte aligned; arrays in whole words) when out != 0
-__device__ __forceinline__ uint32_t col_runs(uint64_t *X, uint32_t n, uint32_t lane) {
-    uint32_t r = 0, last = 0xFFFFFFFEu;
-#pragma unroll 1
-    for (uint32_t e = 0; e < n; e++) {
-        const uint32_t v = col(X, e, lane);
-        r += (v != last + 1);
-        last = v;
-    }
-    return r;
-}
-__device__ __forceinline__ void col_emit(uint64_t *X, uint32_t n, uint32_t ty, uint8_t *out, uint32_t lane) {
-    if (ty == T_ARRAY) {
-        uint32_t *o = reinterpret_cast<uint32_t *>(out);
-#pragma unroll 1
-        for (uint32_t e = 0; e < n; e += 2)
-            o[e / 2] = (uint32_t)col(X, e, lane) | (e + 1 < n ? (uint32_t)col(X, e + 1, lane) << 16 : 0u);
-    } else {
-        uint32_t *o = reinterpret_cast<uint32_t *>(out);
-        uint32_t k = 0, s = col(X, 0, lane), last = s;
-#pragma unroll 1
-        for (uint32_t e = 1; e < n; e++) {
-            const uint32_t v = col(X, e, lane);
-            if (v != last + 1) {
-                o[k++] = s | ((last - s) << 16);
-                s = v;
-            }
-            last = v;
-        }
-        o[k] = s | ((last - s) << 16);
-    }
 }
 
 // T0 = T0 op B_0 op ... op B_{nb-1} over the bitsets at bp[0..nb) (from 0
@@ -388,15 +362,23 @@ __device__ void multi_key_wide(const MParams &P, uint32_t q, const MultiDev &qd,
     __syncwarp();
 }
 
-// The union of the K members' sorted arrays for this lane's key (the
-// containers MS->ix names), written to the lane's column of X; the members'
-// heads stay in registers, each output value takes the smallest and advances
-// every member that holds it.  Returns the number of values.
-template <uint32_t K>
-__device__ __forceinline__ uint32_t kway_merge(const MParams &P, const uint32_t *mem, const MScratch *MS, uint64_t *X,
-                                               uint32_t lane) {
+// One lane's key, merged from its members' containers (staged in the
+// lane's slice of the warp's tiles when they fit, else read in place).
+// EMIT = false counts the result's values n and maximal runs r; with EMIT
+// the result is written to out (4-byte aligned) as type ty: an array as
+// pairs of values per word (zero-padded), runs as start | (length - 1) << 16.
+// The first pass of a key writes the array form while it counts; only a key
+// whose canonical type turns out to be runs is merged a second time.
+
+// OR: the union of the K members' sorted arrays (the containers MS->ix
+// names); the members' heads stay in registers, each output value takes the
+// smallest and advances every member that holds it
+template <uint32_t K, bool EMIT>
+__device__ __forceinline__ void kway_union(const MParams &P, const uint32_t *mem, const MScratch *MS, uint32_t lane,
+                                           const uint16_t *stage, uint32_t ty, uint8_t *out, uint32_t &n,
+                                           uint32_t &r) {
     const uint16_t *ap[K];
-    uint32_t len[K], at[K], head[K];
+    uint32_t len[K], at[K], head[K], w = 0;
 #pragma unroll
     for (uint32_t i = 0; i < K; i++) {
         ap[i] = nullptr;
@@ -406,26 +388,128 @@ __device__ __forceinline__ uint32_t kway_merge(const MParams &P, const uint32_t 
         if (j != NOIX) {
             const BmView V = P.pool[mem[i]];
             const uint64_t d = __ldg(V.descs + j);
-            ap[i] = reinterpret_cast<const uint16_t *>(V.base + d_off(d));
             len[i] = d_card(d);
-            head[i] = __ldg(ap[i]);
+            ap[i] = stage ? stage + 2 * w : reinterpret_cast<const uint16_t *>(V.base + d_off(d));
+            w += (len[i] + 1) / 2;
+            head[i] = ap[i][0];
         }
     }
-    uint32_t n = 0;
+    uint32_t *o32 = reinterpret_cast<uint32_t *>(out);
+    uint32_t last = 0xFFFFFFFEu, rs = 0, pend = 0;
+    n = 0;
+    r = 0;
     for (;;) {
         uint32_t v = MKEY_END;
 #pragma unroll
         for (uint32_t i = 0; i < K; i++) v = min(v, head[i]);
         if (v == MKEY_END) break;
-        col(X, n++, lane) = (uint16_t)v;
+        if (v != last + 1) {   // a run starts at v
+            if (EMIT && ty == T_RUN && r) o32[r - 1] = rs | ((last - rs) << 16);
+            rs = v;
+            r++;
+        }
+        if (EMIT && ty == T_ARRAY) {
+            if (n & 1) o32[n >> 1] = pend | (v << 16);
+            else pend = v;
+        }
+        n++;
+        last = v;
 #pragma unroll
         for (uint32_t i = 0; i < K; i++)
             if (head[i] == v) {
                 at[i]++;
-                head[i] = at[i] < len[i] ? (uint32_t)__ldg(ap[i] + at[i]) : MKEY_END;
+                head[i] = at[i] < len[i] ? (uint32_t)ap[i][at[i]] : MKEY_END;
             }
     }
-    return n;
+    if (EMIT && n) {
+        if (ty == T_RUN) o32[r - 1] = rs | ((last - rs) << 16);
+        else if (n & 1) o32[n >> 1] = pend;
+    }
+}
+
+// AND: the values of the smallest array (member min_i) that every other
+// member holds, each found by a binary search from that member's cursor
+template <uint32_t K, bool EMIT>
+__device__ __forceinline__ void and_filter(const MParams &P, const uint32_t *mem, const MScratch *MS, uint32_t min_i,
+                                           uint32_t lane, const uint16_t *stage, uint32_t ty, uint8_t *out,
+                                           uint32_t &n, uint32_t &r) {
+    const uint16_t *ap[K], *A0 = nullptr;
+    uint32_t len[K], from[K], n0 = 0, w = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < K; i++) {
+        const BmView V = P.pool[mem[i]];
+        const uint64_t d = __ldg(V.descs + MS->ix[i][lane]);
+        len[i] = d_card(d);
+        from[i] = 0;
+        ap[i] = stage ? stage + 2 * w : reinterpret_cast<const uint16_t *>(V.base + d_off(d));
+        w += (len[i] + 1) / 2;
+        if (i == min_i) {
+            A0 = ap[i];
+            n0 = len[i];
+        }
+    }
+    uint32_t *o32 = reinterpret_cast<uint32_t *>(out);
+    uint32_t last = 0xFFFFFFFEu, rs = 0, pend = 0;
+    n = 0;
+    r = 0;
+    bool more = true;   // false once some member has no value left above the current one
+#pragma unroll 1
+    for (uint32_t e = 0; e < n0 && more; e++) {
+        const uint32_t v = A0[e];
+        bool keep = true;
+#pragma unroll
+        for (uint32_t i = 0; i < K; i++) {
+            if (i == min_i || !keep) continue;
+            from[i] += lower_bound_gen(ap[i] + from[i], len[i] - from[i], v);
+            keep = from[i] < len[i] && ap[i][from[i]] == v;
+            more = more && from[i] < len[i];
+        }
+        if (!keep) continue;
+        if (v != last + 1) {
+            if (EMIT && ty == T_RUN && r) o32[r - 1] = rs | ((last - rs) << 16);
+            rs = v;
+            r++;
+        }
+        if (EMIT && ty == T_ARRAY) {
+            if (n & 1) o32[n >> 1] = pend | (v << 16);
+            else pend = v;
+        }
+        n++;
+        last = v;
+    }
+    if (EMIT && n) {
+        if (ty == T_RUN) o32[r - 1] = rs | ((last - rs) << 16);
+        else if (n & 1) o32[n >> 1] = pend;
+    }
+}
+
+template <bool EMIT>
+__device__ __forceinline__ void lane_key(const MParams &P, const uint32_t *mem, const MScratch *MS, uint32_t k,
+                                         bool is_and, uint32_t min_i, uint32_t lane, const uint16_t *stage,
+                                         uint32_t ty, uint8_t *out, uint32_t &n, uint32_t &r) {
+    if (is_and) {
+        switch (k) {
+            case 1: and_filter<1, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+            case 2: and_filter<2, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+            case 3: and_filter<3, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+            case 4: and_filter<4, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+            case 5: and_filter<5, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+            case 6: and_filter<6, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+            case 7: and_filter<7, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+            default: and_filter<8, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+        }
+        return;
+    }
+    switch (k) {
+        case 1: kway_union<1, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+        case 2: kway_union<2, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+        case 3: kway_union<3, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+        case 4: kway_union<4, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+        case 5: kway_union<5, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+        case 6: kway_union<6, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+        case 7: kway_union<7, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+        default: kway_union<8, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+    }
 }
 
 __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd, uint32_t local, uint64_t *T0,
@@ -545,66 +629,66 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
         es->keys[qd.slot_base + pos] = (uint16_t)key;
     }
     if (empty) in_acc = 0;   // an absent container ends the key's AND: nothing is read
-    // lane path: the key's result in the lane's column of the two tiles
-    uint64_t *X = T0;
-    uint32_t n = 0;
-    if (lane_path) {
-        if (is_and) {
-            const BmView V0 = P.pool[mem[min_i]];
-            const uint64_t d0 = __ldg(V0.descs + MS->ix[min_i][lane]);
-            const uint16_t *A0 = reinterpret_cast<const uint16_t *>(V0.base + d_off(d0));
-            n = d_card(d0);
-            for (uint32_t e = 0; e < n; e++) col(X, e, lane) = __ldg(A0 + e);
-            for (uint32_t i = 0; i < k && n; i++) {
-                if (i == min_i) continue;
-                const BmView V = P.pool[mem[i]];
-                const uint64_t d = __ldg(V.descs + MS->ix[i][lane]);
-                const uint16_t *A = reinterpret_cast<const uint16_t *>(V.base + d_off(d));
-                const uint32_t na = d_card(d);
-                uint32_t m = 0, from = 0;
-                for (uint32_t e = 0; e < n; e++) {
-                    const uint32_t v = col(X, e, lane);
-                    from += lower_bound_u16(A + from, na - from, v);
-                    if (from < na && __ldg(A + from) == v) col(X, m++, lane) = (uint16_t)v;
-                }
-                n = m;
+    // lane path: the key merged by its own lane.  Its arrays are staged in
+    // the lane's 512-byte slice of the warp's tiles when they fit (every
+    // lane's words requested at once with cp.async), else read in place; a
+    // materialised key is written straight to its output, reserved at the
+    // size of its largest possible array (within the batch's output bound),
+    // while it is counted.
+    const uint16_t *stage = nullptr;
+    if (__any_sync(FULL, lane_path)) {
+        if (lane_path) {
+            uint32_t words = 0;
+            for (uint32_t i = 0; i < k; i++) {
+                const uint32_t j = MS->ix[i][lane];
+                if (j != NOIX) words += (d_card(__ldg(P.pool[mem[i]].descs + j)) + 1) / 2;
             }
-        } else {
-            // one k-way merge of the key's sorted arrays, duplicates once,
-            // compiled for each member count
-            switch (k) {
-                case 1: n = kway_merge<1>(P, mem, MS, X, lane); break;
-                case 2: n = kway_merge<2>(P, mem, MS, X, lane); break;
-                case 3: n = kway_merge<3>(P, mem, MS, X, lane); break;
-                case 4: n = kway_merge<4>(P, mem, MS, X, lane); break;
-                case 5: n = kway_merge<5>(P, mem, MS, X, lane); break;
-                case 6: n = kway_merge<6>(P, mem, MS, X, lane); break;
-                case 7: n = kway_merge<7>(P, mem, MS, X, lane); break;
-                default: n = kway_merge<8>(P, mem, MS, X, lane); break;
+            if (words <= LSLICE_WORDS) {
+                uint32_t *S = reinterpret_cast<uint32_t *>(T0) + lane * LSLICE_WORDS;
+                uint32_t w = 0;
+                for (uint32_t i = 0; i < k; i++) {
+                    const uint32_t j = MS->ix[i][lane];
+                    if (j == NOIX) continue;
+                    const BmView V = P.pool[mem[i]];
+                    const uint64_t d = __ldg(V.descs + j);
+                    const uint32_t *src = reinterpret_cast<const uint32_t *>(V.base + d_off(d));
+                    const uint32_t nw = (d_card(d) + 1) / 2;
+#pragma unroll 1
+                    for (uint32_t x = 0; x < nw; x++) cp_async4(S + w + x, src + x);
+                    w += nw;
+                }
+                stage = reinterpret_cast<const uint16_t *>(S);
             }
         }
+        cp_async_wait_all();
+        __syncwarp();
     }
-    uint32_t r = 0, ty = T_ARRAY, bytes = 0;
-    if (lane_path && n) {
-        r = col_runs(X, n, lane);
-        ty = canon_type(n, r);   // n <= LCAP: array or runs
-        if (!qd.count_only) bytes = word_alloc_bytes(ty, n, r);
-    }
-    unsigned long long card_acc = lane_path ? n : 0, words_acc = bytes;
+    uint32_t n = 0, r = 0, bytes = 0;
+    if (lane_path && !qd.count_only) bytes = (2 * (is_and ? min_card : sum_card) + 3) & ~3u;
+    unsigned long long card_acc = 0, words_acc = 0;
     uint32_t bits_acc = 0;
-    if (!qd.count_only) {
+    if (qd.count_only) {
+        if (lane_path) lane_key<false>(P, mem, MS, k, is_and, min_i, lane, stage, 0, nullptr, n, r);
+        card_acc = n;
+    } else {
         const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
         uint64_t base = ALLOC_FAIL;
         if (total) base = alloc_w(es, total, lane);
         if (lane_path) {
             uint64_t desc = DESC_EMPTY;
-            if (n && base != ALLOC_FAIL) {
+            if (base != ALLOC_FAIL) {
                 const uint64_t off = base + incl - bytes;
-                col_emit(X, n, ty, es->arena + off, lane);
-                desc = mk_desc(n, ty, ty == T_RUN ? r : 0, off);
-            } else {
-                card_acc = 0;
-                words_acc = 0;
+                lane_key<true>(P, mem, MS, k, is_and, min_i, lane, stage, T_ARRAY, es->arena + off, n, r);
+                if (n) {
+                    const uint32_t ty = canon_type(n, r);   // n <= LCAP <= 4096: array or runs
+                    if (ty == T_RUN) {
+                        uint32_t n2, r2;
+                        lane_key<true>(P, mem, MS, k, is_and, min_i, lane, stage, T_RUN, es->arena + off, n2, r2);
+                    }
+                    desc = mk_desc(n, ty, ty == T_RUN ? r : 0, off);
+                    card_acc = n;
+                    words_acc = word_alloc_bytes(ty, n, r);
+                }
             }
             es->descs[qd.slot_base + pos] = desc;
             es->keys[qd.slot_base + pos] = (uint16_t)key;
