@@ -119,7 +119,7 @@ __device__ uint64_t alloc_b(MState *es, uint32_t lane) {
 // straight into its output; the other keys are folded by the whole warp in
 // the tiles, as the general path does.
 constexpr uint32_t MK = 8;
-constexpr uint32_t LCAP = 256;   // values in play that one lane merges alone (the rest: the warp, in tiles)
+constexpr uint32_t LCAP = 1024;  // values in play that one lane merges alone (the rest: the warp, in tiles)
 constexpr uint32_t LSLICE_WORDS = 128;   // a lane's staging slice of the warp's two tiles (32 x 512 B = 16 KB)
 constexpr uint32_t NOIX = 0xFFFFFFFFu;
 constexpr uint32_t MKEY_END = 0x10000u;
@@ -173,6 +173,45 @@ __device__ __forceinline__ uint32_t lower_bound_u16(const uint16_t *a, uint32_t 
         else hi = m;
     }
     return lo;
+}
+
+// first index i of sorted keys[0..n) with keys[i] >= key, searched from the
+// position key would have if the n keys were spread evenly over [0, 65536):
+// a gallop away from that guess brackets the answer, then a binary search
+// in the bracket (a few loads for evenly spread keys, O(log n) at worst)
+__device__ __forceinline__ uint32_t lower_bound_interp(const uint16_t *keys, uint32_t n, uint32_t key) {
+    if (n == 0) return 0;
+    uint32_t g = (uint32_t)(((uint64_t)key * n) >> 16);
+    if (g >= n) g = n - 1;
+    uint32_t lo, hi;   // the answer is in [lo, hi]
+    if ((uint32_t)__ldg(keys + g) < key) {
+        lo = g + 1;
+        hi = n;
+        uint32_t step = 1;
+#pragma unroll 1
+        while (lo + step - 1 < n) {
+            if ((uint32_t)__ldg(keys + lo + step - 1) >= key) {
+                hi = lo + step - 1;
+                break;
+            }
+            lo += step;
+            step <<= 1;
+        }
+    } else {
+        hi = g;
+        lo = 0;
+        uint32_t step = 1;
+#pragma unroll 1
+        while (hi >= step) {
+            if ((uint32_t)__ldg(keys + hi - step) < key) {
+                lo = hi - step + 1;
+                break;
+            }
+            hi -= step;
+            step <<= 1;
+        }
+    }
+    return lo + lower_bound16(keys + lo, hi - lo, key);
 }
 
 // first index i >= start of sorted keys[0..n) with keys[i] >= key, looking at
@@ -565,7 +604,7 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
         // each member's keys in [k_lo, k_hi]: continuing tiles start where the
         // previous tile's range ended
         const BmView V = P.pool[mem[lane]];
-        const uint32_t lo = cont ? lb_from(V.keys, V.n, MS->hi[lane], k_lo) : lower_bound16(V.keys, V.n, k_lo);
+        const uint32_t lo = cont ? lb_from(V.keys, V.n, MS->hi[lane], k_lo) : lower_bound_interp(V.keys, V.n, k_lo);
         MS->lo[lane] = lo;
         MS->hi[lane] = lb_from(V.keys, V.n, lo, k_hi + 1);
     }
