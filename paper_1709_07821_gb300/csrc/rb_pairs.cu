@@ -94,7 +94,8 @@ struct ExecState {
     unsigned long long small_cap, small_n1, small_n2, swork1, swork2;
     unsigned long long lean_bytes, heavy_bytes, small_bytes;
     unsigned long long cwork;   // k_compact's query counter
-    unsigned int status, pad;
+    unsigned int status;
+    unsigned int wchunk;        // bytes of a per-warp word chunk (a power of two)
 };
 
 // both input views of a query, so that a kernel reads them without first
@@ -141,17 +142,20 @@ __device__ __forceinline__ uint64_t alloc_bitset_warp(ExecState *es, uint32_t la
     return es->bits_off + old;
 }
 
-// Word-region allocation for k_lean: each warp takes WCHUNK bytes at a time
-// from the shared counter and hands them out itself (state in shared memory,
-// wa[0] = next free offset, wa[1] = end of the warp's chunk; wa[2], wa[3]
-// gather the current query's cardinality and word bytes); requests above
-// WDIRECT go to the counter directly.  A chunk is abandoned only when a
-// request of at most WDIRECT does not fit, so at most 1/8 of the chunked bytes
-// plus one chunk per warp go unused; the arena adds that much slack.
+// Word-region allocation for k_lean: each warp takes a chunk of es->wchunk
+// bytes at a time from the shared counter and hands it out itself (state in
+// shared memory, wa[0] = next free offset, wa[1] = end of the warp's chunk;
+// wa[2], wa[3] gather the current query's cardinality and word bytes);
+// requests above 1/8 of a chunk go to the counter directly.  A chunk is
+// abandoned only when a request of at most 1/8 of a chunk does not fit, so at
+// most 1/8 of the chunked bytes plus one chunk per warp go unused; the arena
+// adds that much slack.  The chunk is sized per plan (word_chunk): a batch
+// with tens of GB of results refills from the one counter millions of times
+// with small chunks, and those same-address atomics serialise.
 // Returns the offset within the word region (warp-uniform), or ALLOC_FAIL
 // after flagging the overflow.
-constexpr uint32_t WCHUNK = 16384;
-constexpr uint32_t WDIRECT = WCHUNK / 8;
+constexpr uint32_t WCHUNK_MIN = 16384;
+constexpr uint32_t WCHUNK_MAX = 131072;
 __device__ __forceinline__ uint64_t lean_alloc(ExecState *es, unsigned long long *wa, uint32_t bytes,
                                                uint32_t lane) {
     unsigned long long r = 0;
@@ -160,17 +164,20 @@ __device__ __forceinline__ uint64_t lean_alloc(ExecState *es, unsigned long long
         if (cur + bytes <= end) {
             r = cur;
             wa[0] = cur + bytes;
-        } else if (bytes > WDIRECT) {
-            r = atomicAdd(&es->words_used, (unsigned long long)bytes);
-            if (r + bytes > es->words_cap) r = ALLOC_FAIL;
         } else {
-            r = atomicAdd(&es->words_used, (unsigned long long)WCHUNK);
-            if (r + WCHUNK > es->words_cap) {
-                r = ALLOC_FAIL;
-                wa[0] = wa[1] = 0;
+            const uint32_t wchunk = es->wchunk;
+            if (bytes > (wchunk >> 3)) {
+                r = atomicAdd(&es->words_used, (unsigned long long)bytes);
+                if (r + bytes > es->words_cap) r = ALLOC_FAIL;
             } else {
-                wa[0] = r + bytes;
-                wa[1] = r + WCHUNK;
+                r = atomicAdd(&es->words_used, (unsigned long long)wchunk);
+                if (r + wchunk > es->words_cap) {
+                    r = ALLOC_FAIL;
+                    wa[0] = wa[1] = 0;
+                } else {
+                    wa[0] = r + bytes;
+                    wa[1] = r + wchunk;
+                }
             }
         }
         if (r == ALLOC_FAIL) atomicOr(&es->status, 1u);
@@ -189,8 +196,9 @@ __device__ __forceinline__ uint64_t chunk_alloc_words(ExecState *es, WChunk &w, 
         w.cur += bytes;
         return es->words_off + r;
     }
-    const bool direct = bytes > WDIRECT;
-    const uint32_t take = direct ? bytes : WCHUNK;
+    const uint32_t wchunk = es->wchunk;
+    const bool direct = bytes > (wchunk >> 3);
+    const uint32_t take = direct ? bytes : wchunk;
     unsigned long long old = 0;
     if (lane == 0) old = atomicAdd(&es->words_used, (unsigned long long)take);
     old = __shfl_sync(FULL, old, 0);
@@ -201,7 +209,7 @@ __device__ __forceinline__ uint64_t chunk_alloc_words(ExecState *es, WChunk &w, 
     }
     if (!direct) {
         w.cur = old + bytes;
-        w.end = old + WCHUNK;
+        w.end = old + wchunk;
     }
     return es->words_off + old;
 }
@@ -1959,8 +1967,19 @@ cudaError_t enqueue_run(rb_plan *p, const rb_schedule &sc, cudaStream_t s, bool 
 struct ArenaLayout {
     uint64_t o_keys, o_defer, o_small, o_words, o_bits, bytes;
     uint64_t words_cap;   // word region incl. the slack of k_lean's per-warp chunks
+    uint32_t wchunk;      // bytes of one per-warp word chunk
     uint64_t bits_cap;    // bitset region incl. the slack of k_heavy's per-warp chunks
 };
+
+// The per-warp word chunk: the largest power of two in [WCHUNK_MIN,
+// WCHUNK_MAX] whose one unfinished chunk per warp stays within 1/16 of the
+// word bytes the plan expects (small batches keep small chunks and small
+// arenas; large ones refill from the shared counter rarely)
+uint32_t word_chunk(uint64_t words, uint64_t warps) {
+    uint32_t c = WCHUNK_MAX;
+    while (c > WCHUNK_MIN && (uint64_t)c * warps * 16 > words) c >>= 1;
+    return c;
+}
 
 ArenaLayout arena_layout(const rb_plan *p) {
     ArenaLayout L;
@@ -1970,7 +1989,9 @@ ArenaLayout arena_layout(const rb_plan *p) {
     L.o_small = align_up(L.o_defer + sizeof(Deferred) * p->defer_cap, 256);
     L.o_words = align_up(L.o_small + sizeof(Item) * p->small_cap, 256);
     const rb_schedule sc = current_schedule();
-    L.words_cap = p->words_cap + p->words_cap / 7 + (lean_warps(p, sc) + heavy_warps(p, sc)) * WCHUNK;
+    const uint64_t warps = lean_warps(p, sc) + heavy_warps(p, sc);
+    L.wchunk = word_chunk(p->words_cap, warps);
+    L.words_cap = p->words_cap + p->words_cap / 7 + warps * L.wchunk;
     L.o_bits = align_up(L.o_words + L.words_cap, 256);
     L.bits_cap = p->bits_cap + heavy_warps(p, current_schedule()) * (HCHUNK - 1) * 8192ull;
     L.bytes = L.o_bits + L.bits_cap;
@@ -2000,6 +2021,7 @@ rb_status run_launch(rb_plan *p, cudaStream_t s, bool graph, RbArena **arena) {
     h.small_cap = p->small_cap;
     h.words_off = L.o_words;
     h.words_cap = L.words_cap;
+    h.wchunk = L.wchunk;
     h.bits_off = L.o_bits;
     h.bits_cap = L.bits_cap;
     cudaError_t e = cudaSuccess;
