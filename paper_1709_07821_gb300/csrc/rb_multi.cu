@@ -115,12 +115,12 @@ __device__ uint64_t alloc_b(MState *es, uint32_t lane) {
 // output key).  A key whose containers are all arrays with at most LCAP
 // values in play is then merged by its own lane (OR: one k-way merge of the
 // sorted arrays; AND: the smallest array filtered by binary search in the
-// others) from its arrays staged in the lane's slice of the warp's tiles,
+// others) from its arrays staged in its share of the warp's tiles,
 // straight into its output; the other keys are folded by the whole warp in
 // the tiles, as the general path does.
 constexpr uint32_t MK = 8;
 constexpr uint32_t LCAP = 1024;  // values in play that one lane merges alone (the rest: the warp, in tiles)
-constexpr uint32_t LSLICE_WORDS = 128;   // a lane's staging slice of the warp's two tiles (32 x 512 B = 16 KB)
+constexpr uint32_t STAGE_WORDS = 4096;   // the warp's two tiles, shared out to its lanes by a prefix sum
 constexpr uint32_t NOIX = 0xFFFFFFFFu;
 constexpr uint32_t MKEY_END = 0x10000u;
 
@@ -402,7 +402,7 @@ __device__ void multi_key_wide(const MParams &P, uint32_t q, const MultiDev &qd,
 }
 
 // One lane's key, merged from its members' containers (staged in the
-// lane's slice of the warp's tiles when they fit, else read in place).
+// lane's share of the warp's tiles when they fit, else read in place).
 // EMIT = false counts the result's values n and maximal runs r; with EMIT
 // the result is written to out (4-byte aligned) as type ty: an array as
 // pairs of values per word (zero-padded), runs as start | (length - 1) << 16.
@@ -669,35 +669,36 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
     }
     if (empty) in_acc = 0;   // an absent container ends the key's AND: nothing is read
     // lane path: the key merged by its own lane.  Its arrays are staged in
-    // the lane's 512-byte slice of the warp's tiles when they fit (every
-    // lane's words requested at once with cp.async), else read in place; a
+    // the warp's tiles, packed lane after lane by a prefix sum of their words
+    // (every lane's words requested at once with cp.async; consecutive lanes
+    // start in different banks), when they fit, else read in place; a
     // materialised key is written straight to its output, reserved at the
     // size of its largest possible array (within the batch's output bound),
     // while it is counted.
     const uint16_t *stage = nullptr;
     if (__any_sync(FULL, lane_path)) {
-        if (lane_path) {
-            uint32_t words = 0;
+        uint32_t words = 0;
+        if (lane_path)
             for (uint32_t i = 0; i < k; i++) {
                 const uint32_t j = MS->ix[i][lane];
                 if (j != NOIX) words += (d_card(__ldg(P.pool[mem[i]].descs + j)) + 1) / 2;
             }
-            if (words <= LSLICE_WORDS) {
-                uint32_t *S = reinterpret_cast<uint32_t *>(T0) + lane * LSLICE_WORDS;
-                uint32_t w = 0;
-                for (uint32_t i = 0; i < k; i++) {
-                    const uint32_t j = MS->ix[i][lane];
-                    if (j == NOIX) continue;
-                    const BmView V = P.pool[mem[i]];
-                    const uint64_t d = __ldg(V.descs + j);
-                    const uint32_t *src = reinterpret_cast<const uint32_t *>(V.base + d_off(d));
-                    const uint32_t nw = (d_card(d) + 1) / 2;
+        const uint32_t wincl = warp_incl(words, lane);
+        if (lane_path && wincl <= STAGE_WORDS) {
+            uint32_t *S = reinterpret_cast<uint32_t *>(T0) + (wincl - words);
+            uint32_t w = 0;
+            for (uint32_t i = 0; i < k; i++) {
+                const uint32_t j = MS->ix[i][lane];
+                if (j == NOIX) continue;
+                const BmView V = P.pool[mem[i]];
+                const uint64_t d = __ldg(V.descs + j);
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(V.base + d_off(d));
+                const uint32_t nw = (d_card(d) + 1) / 2;
 #pragma unroll 1
-                    for (uint32_t x = 0; x < nw; x++) cp_async4(S + w + x, src + x);
-                    w += nw;
-                }
-                stage = reinterpret_cast<const uint16_t *>(S);
+                for (uint32_t x = 0; x < nw; x++) cp_async4(S + w + x, src + x);
+                w += nw;
             }
+            stage = reinterpret_cast<const uint16_t *>(S);
         }
         cp_async_wait_all();
         __syncwarp();
