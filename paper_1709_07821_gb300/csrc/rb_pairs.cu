@@ -356,8 +356,9 @@ __device__ __forceinline__ uint32_t keep_table(uint32_t op) {
 // step compares the two heads, keeps the smaller one (either one when they
 // are equal, and then both advance) by the op's table, and advances the
 // input(s) it came from; counts cardinality c and runs r, and with EMIT
-// writes the kept values.  a and b are generic pointers: the arrays staged
-// in shared memory, or in global memory.
+// writes the kept values to out (4-byte aligned; whole words are written,
+// the upper half of an odd last word zeroed).  a and b are generic pointers:
+// the arrays staged in shared memory, or in global memory.
 template <bool EMIT>
 __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *a, uint32_t na, const uint16_t *b,
                                                   uint32_t nb, uint32_t &c, uint32_t &r, uint16_t *out) {
@@ -377,7 +378,8 @@ __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *
         const bool lt = va < vb, gt = vb < va;
         const uint32_t v = gt ? vb : va;
         if (lt ? k_a : gt ? k_b : k_ab) {
-            if (EMIT) out[c] = (uint16_t)v;
+            // kept values leave in pairs, one 4-byte store per two values
+            if (EMIT && (c & 1u)) reinterpret_cast<uint32_t *>(out)[c >> 1] = last | (v << 16);
             r += (v != last + 1);
             last = v;
             c++;
@@ -385,6 +387,7 @@ __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *
         i += !gt;
         j += !lt;
     }
+    if (EMIT && (c & 1u)) reinterpret_cast<uint32_t *>(out)[c >> 1] = last;   // zero upper half
 }
 
 // ------------------------------------------------------------ lean kernel
