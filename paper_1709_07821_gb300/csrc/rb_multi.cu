@@ -9,6 +9,7 @@
 // prefix of its word popcounts.  Queries of up to MK members work on tiles
 // of 32 output keys (fast path below); wider ones on one key per tile.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "rb_device.cuh"
@@ -71,19 +72,6 @@ __device__ __forceinline__ void t_apply(uint64_t *T0, const uint64_t *w, uint32_
     __syncwarp();
 }
 
-// fold one container into the accumulator tile T0 (T1 is scratch)
-__device__ void fold_into(uint64_t *T0, uint64_t *T1, const CRef &x, uint32_t op, uint32_t lane) {
-    if (x.type == T_BITSET) {
-        t_apply(T0, reinterpret_cast<const uint64_t *>(x.p), op, lane);
-    } else if (x.type == T_ARRAY && op == OP_OR) {
-        t_or_array(T0, reinterpret_cast<const uint16_t *>(x.p), x.card, lane);
-        __syncwarp();
-    } else {
-        t_decode(T1, x, lane);
-        t_apply(T0, T1, op, lane);
-    }
-}
-
 __device__ uint64_t alloc_w(MState *es, uint32_t bytes, uint32_t lane) {
     unsigned long long old = 0;
     if (lane == 0) old = atomicAdd(&es->words_used, (unsigned long long)bytes);
@@ -120,7 +108,7 @@ __device__ uint64_t alloc_b(MState *es, uint32_t lane) {
 // the tiles, as the general path does.
 constexpr uint32_t MK = 8;
 constexpr uint32_t LCAP = 1024;  // values in play that one lane merges alone (the rest: the warp, in tiles)
-constexpr uint32_t STAGE_WORDS = 4096;   // the warp's two tiles, shared out to its lanes by a prefix sum
+constexpr uint32_t STAGE_WORDS = 2048;   // the warp's tile, shared out to its lanes by a prefix sum
 constexpr uint32_t NOIX = 0xFFFFFFFFu;
 constexpr uint32_t MKEY_END = 0x10000u;
 
@@ -134,7 +122,11 @@ struct MScratch {
     uint32_t c_q, c_next, c_word, pad;
 };
 constexpr uint32_t MCHUNK = 4;   // most consecutive tiles a warp takes at once (large batches)
-constexpr uint32_t WARP_SMEM = 16384 + sizeof(MScratch);
+// one 8 KB tile per warp (lane staging, then the folds) and its scratch;
+// 16 warps per SM at 128 registers per thread (a cap of 102 for 20 warps
+// spills inside the merges and is slower)
+constexpr uint32_t WARP_SMEM = 8192 + sizeof(MScratch);
+constexpr int MULTI_WARPS_PER_SM = 16;
 
 // index of the n-th (from 0) set bit of x, n < popcount(x)
 __device__ __forceinline__ uint32_t nth_set_bit(uint64_t x, uint32_t n) {
@@ -225,6 +217,132 @@ __device__ __forceinline__ uint32_t lb_from(const uint16_t *keys, uint32_t n, ui
     return start + w + lower_bound16(keys + start + w, n - start - w, key);
 }
 
+// The folds below work on the accumulator tile alone (no second tile), so
+// that a warp needs 8 KB of shared memory: word n of a tile holds the values
+// [64n, 64n + 64).
+
+// OR: set the bits of every run [s, e] of a run container; AND: clear every
+// bit outside its runs (the gaps before, between and after them).  Lanes take
+// the ranges in turn; the words a range covers whole are written whole and
+// its edge words by atomics (neighbouring ranges can share an edge word,
+// never a whole word, since runs are maximal).
+template <bool OR>
+__device__ void t_runs_inplace(uint64_t *T, const uint32_t *runs, uint32_t r, uint32_t lane) {
+    unsigned long long *TU = reinterpret_cast<unsigned long long *>(T);
+    const uint32_t n = OR ? r : r + 1;
+#pragma unroll 1
+    for (uint32_t i = lane; i < n; i += 32) {
+        int s, e;   // the range [s, e]; empty when e < s
+        if (OR) {
+            const uint32_t w = __ldg(runs + i);
+            s = (int)(w & 0xFFFFu);
+            e = s + (int)(w >> 16);
+        } else {
+            if (i == 0) {
+                s = 0;
+            } else {
+                const uint32_t w = __ldg(runs + i - 1);
+                s = (int)(w & 0xFFFFu) + (int)(w >> 16) + 1;
+            }
+            e = i == r ? 65535 : (int)(__ldg(runs + i) & 0xFFFFu) - 1;
+        }
+        if (e < s) continue;
+        const uint32_t ws = (uint32_t)s >> 6, we = (uint32_t)e >> 6;
+        const unsigned long long ms = ~0ull << (s & 63), me = ~0ull >> (63 - (e & 63));
+        if (ws == we) {
+            if (OR) atomicOr(TU + ws, ms & me);
+            else atomicAnd(TU + ws, ~(ms & me));
+            continue;
+        }
+        if (OR) atomicOr(TU + ws, ms);
+        else atomicAnd(TU + ws, ~ms);
+#pragma unroll 1
+        for (uint32_t w = ws + 1; w < we; w++) TU[w] = OR ? ~0ull : 0ull;
+        if (OR) atomicOr(TU + we, me);
+        else atomicAnd(TU + we, ~me);
+    }
+    __syncwarp();
+}
+
+// T &= the bits of the sorted array v[0..c): each word is ANDed with the mask
+// of the array's values in its stretch; lane l takes words l, l + 32, ...
+// (consecutive lanes, consecutive words), finding each word's first value by
+// a binary search over the rest of the array from its previous position
+__device__ void t_and_array_inplace(uint64_t *T, const uint16_t *v, uint32_t c, uint32_t lane) {
+    uint32_t j = 0;
+#pragma unroll 1
+    for (uint32_t w = lane; w < 1024; w += 32) {
+        const uint32_t lo = w << 6;
+        j += lower_bound_u16(v + j, c - j, lo);
+        uint64_t m = 0;
+#pragma unroll 1
+        for (; j < c; j++) {
+            const uint32_t x = __ldg(v + j);
+            if (x >= lo + 64) break;
+            m |= 1ull << (x - lo);
+        }
+        T[w] &= m;
+    }
+    __syncwarp();
+}
+
+// fold one container into the accumulator tile T0 (op: AND or OR)
+__device__ void fold_into(uint64_t *T0, const CRef &x, uint32_t op, uint32_t lane) {
+    if (x.type == T_BITSET) {
+        t_apply(T0, reinterpret_cast<const uint64_t *>(x.p), op, lane);
+    } else if (x.type == T_ARRAY) {
+        if (op == OP_OR) {
+            t_or_array(T0, reinterpret_cast<const uint16_t *>(x.p), x.card, lane);
+            __syncwarp();
+        } else {
+            t_and_array_inplace(T0, reinterpret_cast<const uint16_t *>(x.p), x.card, lane);
+        }
+    } else if (op == OP_OR) {
+        t_runs_inplace<true>(T0, reinterpret_cast<const uint32_t *>(x.p), x.runs, lane);
+    } else {
+        t_runs_inplace<false>(T0, reinterpret_cast<const uint32_t *>(x.p), x.runs, lane);
+    }
+}
+
+// run container of r runs from a tile, without scratch: every run start (a
+// set bit after a clear one) goes to the low half of its run's output word,
+// every run end (a set bit before a clear one) to the high half; a last pass
+// turns each word into start | (end - start) << 16
+__device__ __noinline__ void t_emit_runs_direct(const uint64_t *T, uint32_t *out, uint32_t r, uint32_t lane) {
+    uint16_t *o16 = reinterpret_cast<uint16_t *>(out);
+    const ulonglong2 *T2 = reinterpret_cast<const ulonglong2 *>(T);
+    uint32_t bs = 0, be = 0, carry = 0;
+#pragma unroll 1
+    for (int k = 0; k < 16; k++) {
+        const ulonglong2 w = T2[32 * k + lane];
+        const uint32_t top = (uint32_t)(w.y >> 63);
+        uint32_t prev = __shfl_up_sync(FULL, top, 1);
+        if (lane == 0) prev = carry;
+        carry = __shfl_sync(FULL, top, 31);
+        const uint64_t sh0 = (w.x << 1) | (uint64_t)prev, sh1 = (w.y << 1) | (w.x >> 63);
+        uint64_t st0 = w.x & ~sh0, st1 = w.y & ~sh1;   // run starts
+        uint64_t gs0 = ~w.x & sh0, gs1 = ~w.y & sh1;   // first clear bit after a run
+        const uint32_t ns = __popcll(st0) + __popcll(st1), ne = __popcll(gs0) + __popcll(gs1);
+        const uint32_t is = warp_incl(ns, lane), ie = warp_incl(ne, lane);
+        uint32_t ps = bs + is - ns, pe = be + ie - ne;
+        bs += __shfl_sync(FULL, is, 31);
+        be += __shfl_sync(FULL, ie, 31);
+        const uint32_t v0 = (uint32_t)(64 * k + 2 * lane) * 64u;
+        while (st0) { o16[2 * ps++] = (uint16_t)(v0 + __ffsll((long long)st0) - 1); st0 &= st0 - 1; }
+        while (st1) { o16[2 * ps++] = (uint16_t)(v0 + 64 + __ffsll((long long)st1) - 1); st1 &= st1 - 1; }
+        while (gs0) { o16[2 * pe++ + 1] = (uint16_t)(v0 + __ffsll((long long)gs0) - 2); gs0 &= gs0 - 1; }
+        while (gs1) { o16[2 * pe++ + 1] = (uint16_t)(v0 + 64 + __ffsll((long long)gs1) - 2); gs1 &= gs1 - 1; }
+    }
+    if (carry && lane == 0) o16[2 * be + 1] = 65535;   // the last run reaches the end of the chunk
+    __syncwarp();   // the halves written by other lanes are visible from here
+#pragma unroll 1
+    for (uint32_t i = lane; i < r; i += 32) {
+        const uint32_t w = out[i], st = w & 0xFFFFu;
+        out[i] = st | ((((w >> 16) - st) & 0xFFFFu) << 16);
+    }
+    __syncwarp();
+}
+
 // T0 = T0 op B_0 op ... op B_{nb-1} over the bitsets at bp[0..nb) (from 0
 // instead of T0 when from_zero), counting the result's cardinality c and
 // maximal runs r in the same pass; every bitset's words of a stripe are
@@ -261,7 +379,7 @@ __device__ __noinline__ void fuse_bitsets(uint64_t *T0, const uint64_t *const *b
 }
 
 // after the warp folded one key into T0: count, canonical type, emit, record
-__device__ void emit_folded(MState *es, const MultiDev &qd, uint64_t *T0, uint64_t *T1, uint32_t key, uint32_t pos,
+__device__ void emit_folded(MState *es, const MultiDev &qd, uint64_t *T0, uint32_t key, uint32_t pos,
                             unsigned long long &card_acc, unsigned long long &words_acc, uint32_t &bits_acc,
                             uint32_t lane, bool counted = false, uint32_t c = 0, uint32_t r = 0) {
     if (!counted) t_combine<false>(nullptr, T0, T0, OP_OR, c, r, lane);
@@ -286,8 +404,7 @@ __device__ void emit_folded(MState *es, const MultiDev &qd, uint64_t *T0, uint64
                 if (ty == T_ARRAY) {
                     t_emit_array(T0, reinterpret_cast<uint16_t *>(es->arena + off), lane);
                 } else {
-                    uint16_t *S = reinterpret_cast<uint16_t *>(T1);
-                    t_emit_runs(T0, S, S + 2048, reinterpret_cast<uint32_t *>(es->arena + off), r, lane);
+                    t_emit_runs_direct(T0, reinterpret_cast<uint32_t *>(es->arena + off), r, lane);
                 }
                 desc = mk_desc(c, ty, ty == T_RUN ? r : 0, off);
             }
@@ -333,7 +450,7 @@ __device__ __forceinline__ bool out_key(const MParams &P, uint32_t q, const Mult
 // at a time, then the key's containers are folded into T0 one after another
 // (AND: only if every member holds the key) and the result is encoded once.
 __device__ void multi_key_wide(const MParams &P, uint32_t q, const MultiDev &qd, uint32_t p, uint64_t *T0,
-                               uint64_t *T1, uint32_t lane) {
+                               uint32_t lane) {
     const uint32_t *mem = P.members + qd.mbase;
     uint32_t key = 0;
     if (!out_key(P, q, qd, mem, p, key)) return;
@@ -384,13 +501,13 @@ __device__ void multi_key_wide(const MParams &P, uint32_t q, const MultiDev &qd,
             const CRef x = cref(reinterpret_cast<const uint8_t *>(__shfl_sync(FULL, base, src)), ds);
             in_acc += in_payload_bytes(ds) + 15;
             if (is_and && first) t_decode(T0, x, lane);
-            else fold_into(T0, T1, x, qd.op, lane);
+            else fold_into(T0, x, qd.op, lane);
             first = false;
         }
     }
     unsigned long long card_acc = 0, words_acc = 0;
     uint32_t bits_acc = 0;
-    emit_folded(es, qd, T0, T1, key, p, card_acc, words_acc, bits_acc, lane);
+    emit_folded(es, qd, T0, key, p, card_acc, words_acc, bits_acc, lane);
     if (lane == 0) {
         MStats *S = P.stats + q;
         if (card_acc) atomicAdd(&S->card, card_acc);
@@ -401,36 +518,33 @@ __device__ void multi_key_wide(const MParams &P, uint32_t q, const MultiDev &qd,
     __syncwarp();
 }
 
-// One lane's key, merged from its members' containers (staged in the
-// lane's share of the warp's tiles when they fit, else read in place).
+// One lane's key, merged from its members' arrays staged one after another
+// (each padded to whole words) in the warp's tile S from element sbase on.
 // EMIT = false counts the result's values n and maximal runs r; with EMIT
 // the result is written to out (4-byte aligned) as type ty: an array as
 // pairs of values per word (zero-padded), runs as start | (length - 1) << 16.
 // The first pass of a key writes the array form while it counts; only a key
-// whose canonical type turns out to be runs is merged a second time.
+// whose canonical type turns out to be runs is merged a second time.  Each
+// member's state is its cursor and end in S and its head value.
 
 // OR: the union of the K members' sorted arrays (the containers MS->ix
-// names); the members' heads stay in registers, each output value takes the
-// smallest and advances every member that holds it
+// names); each output value takes the smallest head and advances every
+// member that holds it
 template <uint32_t K, bool EMIT>
 __device__ __forceinline__ void kway_union(const MParams &P, const uint32_t *mem, const MScratch *MS, uint32_t lane,
-                                           const uint16_t *stage, uint32_t ty, uint8_t *out, uint32_t &n,
+                                           const uint16_t *S, uint32_t sbase, uint32_t ty, uint8_t *out, uint32_t &n,
                                            uint32_t &r) {
-    const uint16_t *ap[K];
-    uint32_t len[K], at[K], head[K], w = 0;
+    uint32_t at[K], end[K], head[K], w = sbase;
 #pragma unroll
     for (uint32_t i = 0; i < K; i++) {
-        ap[i] = nullptr;
-        len[i] = at[i] = 0;
+        at[i] = end[i] = w;
         head[i] = MKEY_END;
         const uint32_t j = MS->ix[i][lane];
         if (j != NOIX) {
-            const BmView V = P.pool[mem[i]];
-            const uint64_t d = __ldg(V.descs + j);
-            len[i] = d_card(d);
-            ap[i] = stage ? stage + 2 * w : reinterpret_cast<const uint16_t *>(V.base + d_off(d));
-            w += (len[i] + 1) / 2;
-            head[i] = ap[i][0];
+            const uint32_t len = d_card(__ldg(P.pool[mem[i]].descs + j));
+            end[i] = w + len;
+            head[i] = S[w];
+            w += (len + 1) & ~1u;
         }
     }
     uint32_t *o32 = reinterpret_cast<uint32_t *>(out);
@@ -457,7 +571,7 @@ __device__ __forceinline__ void kway_union(const MParams &P, const uint32_t *mem
         for (uint32_t i = 0; i < K; i++)
             if (head[i] == v) {
                 at[i]++;
-                head[i] = at[i] < len[i] ? (uint32_t)ap[i][at[i]] : MKEY_END;
+                head[i] = at[i] < end[i] ? (uint32_t)S[at[i]] : MKEY_END;
             }
     }
     if (EMIT && n) {
@@ -470,22 +584,19 @@ __device__ __forceinline__ void kway_union(const MParams &P, const uint32_t *mem
 // member holds, each found by a binary search from that member's cursor
 template <uint32_t K, bool EMIT>
 __device__ __forceinline__ void and_filter(const MParams &P, const uint32_t *mem, const MScratch *MS, uint32_t min_i,
-                                           uint32_t lane, const uint16_t *stage, uint32_t ty, uint8_t *out,
-                                           uint32_t &n, uint32_t &r) {
-    const uint16_t *ap[K], *A0 = nullptr;
-    uint32_t len[K], from[K], n0 = 0, w = 0;
+                                           uint32_t lane, const uint16_t *S, uint32_t sbase, uint32_t ty,
+                                           uint8_t *out, uint32_t &n, uint32_t &r) {
+    uint32_t at[K], end[K], a0 = 0, n0 = 0, w = sbase;
 #pragma unroll
     for (uint32_t i = 0; i < K; i++) {
-        const BmView V = P.pool[mem[i]];
-        const uint64_t d = __ldg(V.descs + MS->ix[i][lane]);
-        len[i] = d_card(d);
-        from[i] = 0;
-        ap[i] = stage ? stage + 2 * w : reinterpret_cast<const uint16_t *>(V.base + d_off(d));
-        w += (len[i] + 1) / 2;
+        const uint32_t len = d_card(__ldg(P.pool[mem[i]].descs + MS->ix[i][lane]));
+        at[i] = w;
+        end[i] = w + len;
         if (i == min_i) {
-            A0 = ap[i];
-            n0 = len[i];
+            a0 = w;
+            n0 = len;
         }
+        w += (len + 1) & ~1u;
     }
     uint32_t *o32 = reinterpret_cast<uint32_t *>(out);
     uint32_t last = 0xFFFFFFFEu, rs = 0, pend = 0;
@@ -494,14 +605,14 @@ __device__ __forceinline__ void and_filter(const MParams &P, const uint32_t *mem
     bool more = true;   // false once some member has no value left above the current one
 #pragma unroll 1
     for (uint32_t e = 0; e < n0 && more; e++) {
-        const uint32_t v = A0[e];
+        const uint32_t v = S[a0 + e];
         bool keep = true;
 #pragma unroll
         for (uint32_t i = 0; i < K; i++) {
             if (i == min_i || !keep) continue;
-            from[i] += lower_bound_gen(ap[i] + from[i], len[i] - from[i], v);
-            keep = from[i] < len[i] && ap[i][from[i]] == v;
-            more = more && from[i] < len[i];
+            at[i] += lower_bound_gen(S + at[i], end[i] - at[i], v);
+            keep = at[i] < end[i] && S[at[i]] == v;
+            more = more && at[i] < end[i];
         }
         if (!keep) continue;
         if (v != last + 1) {
@@ -524,35 +635,35 @@ __device__ __forceinline__ void and_filter(const MParams &P, const uint32_t *mem
 
 template <bool EMIT>
 __device__ __forceinline__ void lane_key(const MParams &P, const uint32_t *mem, const MScratch *MS, uint32_t k,
-                                         bool is_and, uint32_t min_i, uint32_t lane, const uint16_t *stage,
-                                         uint32_t ty, uint8_t *out, uint32_t &n, uint32_t &r) {
+                                         bool is_and, uint32_t min_i, uint32_t lane, const uint16_t *S,
+                                         uint32_t sbase, uint32_t ty, uint8_t *out, uint32_t &n, uint32_t &r) {
     if (is_and) {
         switch (k) {
-            case 1: and_filter<1, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
-            case 2: and_filter<2, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
-            case 3: and_filter<3, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
-            case 4: and_filter<4, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
-            case 5: and_filter<5, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
-            case 6: and_filter<6, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
-            case 7: and_filter<7, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
-            default: and_filter<8, EMIT>(P, mem, MS, min_i, lane, stage, ty, out, n, r); break;
+            case 1: and_filter<1, EMIT>(P, mem, MS, min_i, lane, S, sbase, ty, out, n, r); break;
+            case 2: and_filter<2, EMIT>(P, mem, MS, min_i, lane, S, sbase, ty, out, n, r); break;
+            case 3: and_filter<3, EMIT>(P, mem, MS, min_i, lane, S, sbase, ty, out, n, r); break;
+            case 4: and_filter<4, EMIT>(P, mem, MS, min_i, lane, S, sbase, ty, out, n, r); break;
+            case 5: and_filter<5, EMIT>(P, mem, MS, min_i, lane, S, sbase, ty, out, n, r); break;
+            case 6: and_filter<6, EMIT>(P, mem, MS, min_i, lane, S, sbase, ty, out, n, r); break;
+            case 7: and_filter<7, EMIT>(P, mem, MS, min_i, lane, S, sbase, ty, out, n, r); break;
+            default: and_filter<8, EMIT>(P, mem, MS, min_i, lane, S, sbase, ty, out, n, r); break;
         }
         return;
     }
     switch (k) {
-        case 1: kway_union<1, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
-        case 2: kway_union<2, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
-        case 3: kway_union<3, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
-        case 4: kway_union<4, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
-        case 5: kway_union<5, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
-        case 6: kway_union<6, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
-        case 7: kway_union<7, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
-        default: kway_union<8, EMIT>(P, mem, MS, lane, stage, ty, out, n, r); break;
+        case 1: kway_union<1, EMIT>(P, mem, MS, lane, S, sbase, ty, out, n, r); break;
+        case 2: kway_union<2, EMIT>(P, mem, MS, lane, S, sbase, ty, out, n, r); break;
+        case 3: kway_union<3, EMIT>(P, mem, MS, lane, S, sbase, ty, out, n, r); break;
+        case 4: kway_union<4, EMIT>(P, mem, MS, lane, S, sbase, ty, out, n, r); break;
+        case 5: kway_union<5, EMIT>(P, mem, MS, lane, S, sbase, ty, out, n, r); break;
+        case 6: kway_union<6, EMIT>(P, mem, MS, lane, S, sbase, ty, out, n, r); break;
+        case 7: kway_union<7, EMIT>(P, mem, MS, lane, S, sbase, ty, out, n, r); break;
+        default: kway_union<8, EMIT>(P, mem, MS, lane, S, sbase, ty, out, n, r); break;
     }
 }
 
 __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd, uint32_t local, uint64_t *T0,
-                                uint64_t *T1, MScratch *MS, uint32_t lane) {
+                                MScratch *MS, uint32_t lane) {
     const uint32_t *mem = P.members + qd.mbase;
     const uint32_t k = qd.k;
     const uint32_t p0 = local * 32u;
@@ -661,30 +772,48 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
         }
     }
     const bool empty = lane < n_act && is_and && present < k;
-    const bool lane_path = lane < n_act && !empty && all_arr && (is_and ? min_card <= LCAP : sum_card <= LCAP);
-    const bool warp_path = lane < n_act && !empty && !lane_path;
+    const bool cand = lane < n_act && !empty && all_arr && (is_and ? min_card <= LCAP : sum_card <= LCAP);
     if (empty && !qd.count_only) {
         es->descs[qd.slot_base + pos] = DESC_EMPTY;
         es->keys[qd.slot_base + pos] = (uint16_t)key;
     }
     if (empty) in_acc = 0;   // an absent container ends the key's AND: nothing is read
-    // lane path: the key merged by its own lane.  Its arrays are staged in
-    // the warp's tiles, packed lane after lane by a prefix sum of their words
+    // lane path: the key merged by its own lane from its arrays staged in the
+    // warp's tile, packed lane after lane by a prefix sum of their words
     // (every lane's words requested at once with cp.async; consecutive lanes
-    // start in different banks), when they fit, else read in place; a
-    // materialised key is written straight to its output, reserved at the
-    // size of its largest possible array (within the batch's output bound),
-    // while it is counted.
-    const uint16_t *stage = nullptr;
-    if (__any_sync(FULL, lane_path)) {
-        uint32_t words = 0;
-        if (lane_path)
-            for (uint32_t i = 0; i < k; i++) {
-                const uint32_t j = MS->ix[i][lane];
-                if (j != NOIX) words += (d_card(__ldg(P.pool[mem[i]].descs + j)) + 1) / 2;
-            }
-        const uint32_t wincl = warp_incl(words, lane);
-        if (lane_path && wincl <= STAGE_WORDS) {
+    // start in different banks).  The lanes whose words fit are staged and
+    // merged, then the rest in further rounds (the first waiting lane always
+    // fits, so each round serves at least one); only a key whose arrays alone
+    // pass the tile's size goes to the warp path.  A materialised key is
+    // written straight to its output, reserved for the whole tile before the
+    // rounds at the size of each key's largest possible array (within the
+    // batch's output bound), while it is counted.
+    const uint16_t *stage = reinterpret_cast<const uint16_t *>(T0);
+    uint32_t words = 0;
+    if (cand)
+        for (uint32_t i = 0; i < k; i++) {
+            const uint32_t j = MS->ix[i][lane];
+            if (j != NOIX) words += (d_card(__ldg(P.pool[mem[i]].descs + j)) + 1) / 2;
+        }
+    const bool lane_path = cand && words <= STAGE_WORDS;
+    const bool warp_path = lane < n_act && !empty && !lane_path;
+    unsigned long long card_acc = 0, words_acc = 0;
+    uint32_t bits_acc = 0;
+    uint32_t bytes = 0, oincl = 0;
+    uint64_t obase = ALLOC_FAIL;
+    if (lane_path && !qd.count_only) bytes = (2 * (is_and ? min_card : sum_card) + 3) & ~3u;
+    if (!qd.count_only && __any_sync(FULL, lane_path)) {
+        oincl = warp_incl(bytes, lane);
+        const uint32_t total = __shfl_sync(FULL, oincl, 31);
+        if (total) obase = alloc_w(es, total, lane);
+    }
+    bool pending = lane_path;
+#pragma unroll 1
+    while (__any_sync(FULL, pending)) {
+        const uint32_t wincl = warp_incl(pending ? words : 0u, lane);
+        const bool now = pending && wincl <= STAGE_WORDS;
+        uint32_t sbase = 0;
+        if (now) {
             uint32_t *S = reinterpret_cast<uint32_t *>(T0) + (wincl - words);
             uint32_t w = 0;
             for (uint32_t i = 0; i < k; i++) {
@@ -698,53 +827,48 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
                 for (uint32_t x = 0; x < nw; x++) cp_async4(S + w + x, src + x);
                 w += nw;
             }
-            stage = reinterpret_cast<const uint16_t *>(S);
+            sbase = 2 * (wincl - words);
         }
         cp_async_wait_all();
         __syncwarp();
-    }
-    uint32_t n = 0, r = 0, bytes = 0;
-    if (lane_path && !qd.count_only) bytes = (2 * (is_and ? min_card : sum_card) + 3) & ~3u;
-    unsigned long long card_acc = 0, words_acc = 0;
-    uint32_t bits_acc = 0;
-    if (qd.count_only) {
-        if (lane_path) lane_key<false>(P, mem, MS, k, is_and, min_i, lane, stage, 0, nullptr, n, r);
-        card_acc = n;
-    } else {
-        const uint32_t incl = warp_incl(bytes, lane), total = __shfl_sync(FULL, incl, 31);
-        uint64_t base = ALLOC_FAIL;
-        if (total) base = alloc_w(es, total, lane);
-        if (lane_path) {
-            uint64_t desc = DESC_EMPTY;
-            if (base != ALLOC_FAIL) {
-                const uint64_t off = base + incl - bytes;
-                lane_key<true>(P, mem, MS, k, is_and, min_i, lane, stage, T_ARRAY, es->arena + off, n, r);
-                if (n) {
-                    const uint32_t ty = canon_type(n, r);   // n <= LCAP <= 4096: array or runs
-                    if (ty == T_RUN) {
-                        uint32_t n2, r2;
-                        lane_key<true>(P, mem, MS, k, is_and, min_i, lane, stage, T_RUN, es->arena + off, n2, r2);
+        if (now) {
+            uint32_t n = 0, r = 0;
+            if (qd.count_only) {
+                lane_key<false>(P, mem, MS, k, is_and, min_i, lane, stage, sbase, 0, nullptr, n, r);
+                card_acc += n;
+            } else {
+                uint64_t desc = DESC_EMPTY;
+                if (obase != ALLOC_FAIL) {
+                    const uint64_t off = obase + oincl - bytes;
+                    lane_key<true>(P, mem, MS, k, is_and, min_i, lane, stage, sbase, T_ARRAY, es->arena + off, n, r);
+                    if (n) {
+                        const uint32_t ty = canon_type(n, r);   // n <= LCAP <= 4096: array or runs
+                        if (ty == T_RUN) {
+                            uint32_t n2, r2;
+                            lane_key<true>(P, mem, MS, k, is_and, min_i, lane, stage, sbase, T_RUN, es->arena + off,
+                                           n2, r2);
+                        }
+                        desc = mk_desc(n, ty, ty == T_RUN ? r : 0, off);
+                        card_acc += n;
+                        words_acc += word_alloc_bytes(ty, n, r);
                     }
-                    desc = mk_desc(n, ty, ty == T_RUN ? r : 0, off);
-                    card_acc = n;
-                    words_acc = word_alloc_bytes(ty, n, r);
                 }
+                es->descs[qd.slot_base + pos] = desc;
+                es->keys[qd.slot_base + pos] = (uint16_t)key;
             }
-            es->descs[qd.slot_base + pos] = desc;
-            es->keys[qd.slot_base + pos] = (uint16_t)key;
         }
+        __syncwarp();   // the tile is staged again in the next round
+        pending = pending && !now;
     }
-    __syncwarp();
-    // warp path: one key at a time in the tiles
+    // warp path: one key at a time in the tile
     uint32_t wl = __ballot_sync(FULL, warp_path);
     while (wl) {
         const int src = __ffs(wl) - 1;
         wl &= wl - 1;
         const uint32_t k_key = __shfl_sync(FULL, key, src), k_pos = __shfl_sync(FULL, pos, src);
-        const uint32_t k_min = __shfl_sync(FULL, min_i, src);
-        // arrays and runs are folded into T0 one by one; the bitsets are
-        // combined in one pass at the end, which also counts the result
-        // (AND starts from the smallest container unless it is a bitset)
+        // arrays and runs are folded into T0 one by one (AND starts from the
+        // first of them); the bitsets are combined in one pass at the end,
+        // which also counts the result
         uint32_t nb = 0;
         bool started = false;
         for (uint32_t i = 0; i < k; i++) {
@@ -761,20 +885,20 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
                 } else {
                     t_zero(T0, lane);
                     __syncwarp();
-                    fold_into(T0, T1, x, OP_OR, lane);
+                    fold_into(T0, x, OP_OR, lane);
                 }
                 started = true;
             } else {
-                fold_into(T0, T1, x, is_and ? OP_AND : OP_OR, lane);
+                fold_into(T0, x, is_and ? OP_AND : OP_OR, lane);
             }
         }
         __syncwarp();
         uint32_t c = 0, r = 0;
         if (nb) {
             fuse_bitsets(T0, MS->bp, nb, is_and ? OP_AND : OP_OR, !started, c, r, lane);
-            emit_folded(es, qd, T0, T1, k_key, k_pos, card_acc, words_acc, bits_acc, lane, true, c, r);
+            emit_folded(es, qd, T0, k_key, k_pos, card_acc, words_acc, bits_acc, lane, true, c, r);
         } else {
-            emit_folded(es, qd, T0, T1, k_key, k_pos, card_acc, words_acc, bits_acc, lane);
+            emit_folded(es, qd, T0, k_key, k_pos, card_acc, words_acc, bits_acc, lane);
         }
     }
     // per-query sums
@@ -793,12 +917,11 @@ __device__ void multi_tile_fast(const MParams &P, uint32_t q, const MultiDev &qd
 }
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) k_multi(MParams P) {
+__global__ void __launch_bounds__(WARPS * 32, MULTI_WARPS_PER_SM / WARPS) k_multi(MParams P) {
     extern __shared__ __align__(16) uint64_t smem[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t *T0 = smem + (size_t)warp * (WARP_SMEM / 8);
-    uint64_t *T1 = T0 + 1024;
-    MScratch *MS = reinterpret_cast<MScratch *>(T0 + 2048);
+    MScratch *MS = reinterpret_cast<MScratch *>(T0 + 1024);
     if (lane == 0) MS->c_q = 0xFFFFFFFFu;
     __syncwarp();
     unsigned long long t = 0, t_end = 0, q_lo = 0, q_hi = 0;
@@ -823,8 +946,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_multi(MParams P) {
         }
         const MultiDev qd = P.qs[q];
         const uint32_t local = (uint32_t)(t - q_lo);
-        if (qd.k <= MK) multi_tile_fast(P, q, qd, local, T0, T1, MS, lane);
-        else multi_key_wide(P, q, qd, local, T0, T1, lane);
+        if (qd.k <= MK) multi_tile_fast(P, q, qd, local, T0, MS, lane);
+        else multi_key_wide(P, q, qd, local, T0, lane);
         __syncwarp();
         t++;
     }
@@ -1107,13 +1230,20 @@ rb_status multi_prepare(const rb *const *pool, const BmView *d_pool, uint32_t po
     return RB_OK;
 }
 
+// k_multi is persistent: as many CTAs per SM as fit (found once from the
+// occupancy calculator; 16 warps per SM), capped by the batch's tiles
 template <int W>
-static void launch_multi_w(const MParams &P, int ctas, cudaStream_t s) {
-    static bool attr = false;
+static void launch_multi_w(const MParams &P, cudaStream_t s) {
+    static std::atomic<int> per_sm{0};
     const int smem = W * WARP_SMEM;
-    if (!attr) {
+    int ctas = per_sm.load();
+    if (ctas == 0) {
         cudaFuncSetAttribute(k_multi<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_multi<W>, W * 32, smem) != cudaSuccess || ctas < 1) {
+            cudaGetLastError();
+            ctas = 1;
+        }
+        per_sm.store(ctas);
     }
     unsigned long long need = (P.n_tiles + W - 1) / W, cap = (unsigned long long)sm_count() * ctas;
     unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min(need, cap));
@@ -1166,9 +1296,9 @@ rb_status multi_enqueue(MultiBatch *b, RbArena *arena, cudaStream_t s) {
     const rb_schedule sc = current_schedule();
     if (b->total_tiles) {
         switch (sc.warps_per_cta) {
-            case 2: launch_multi_w<2>(P, sc.ctas_per_sm, s); break;
-            case 8: launch_multi_w<8>(P, sc.ctas_per_sm, s); break;
-            default: launch_multi_w<4>(P, sc.ctas_per_sm, s); break;
+            case 2: launch_multi_w<2>(P, s); break;
+            case 8: launch_multi_w<8>(P, s); break;
+            default: launch_multi_w<4>(P, s); break;
         }
     }
     if (b->any_mat) {
