@@ -345,26 +345,32 @@ __device__ __noinline__ void t_emit_runs_direct(const uint64_t *T, uint32_t *out
 
 // T0 = T0 op B_0 op ... op B_{nb-1} over the bitsets at bp[0..nb) (from 0
 // instead of T0 when from_zero), counting the result's cardinality c and
-// maximal runs r in the same pass; every bitset's words of a stripe are
-// requested together, so the members' loads overlap
+// maximal runs r in the same pass; the members' words of a stripe are
+// requested four members at a time, so their loads overlap
 __device__ __noinline__ void fuse_bitsets(uint64_t *T0, const uint64_t *const *bp, uint32_t nb, uint32_t op,
                                           bool from_zero, uint32_t &c, uint32_t &r, uint32_t lane) {
     ulonglong2 *D = reinterpret_cast<ulonglong2 *>(T0);
     uint32_t cc = 0, rr = 0, carry = 0;
-#pragma unroll 2
+#pragma unroll 1
     for (int k = 0; k < 16; k++) {
-        ulonglong2 y[MK];
-#pragma unroll
-        for (uint32_t m = 0; m < MK; m++)
-            if (m < nb) y[m] = __ldg(reinterpret_cast<const ulonglong2 *>(bp[m]) + 32 * k + lane);
         ulonglong2 x = from_zero ? make_ulonglong2(op == OP_AND ? ~0ull : 0ull, op == OP_AND ? ~0ull : 0ull)
                                  : D[32 * k + lane];
+        // four members' words requested together (eight at once needed
+        // more registers than the kernel's occupancy allows)
 #pragma unroll
-        for (uint32_t m = 0; m < MK; m++)
-            if (m < nb) {
-                x.x = apply_op(op, x.x, y[m].x);
-                x.y = apply_op(op, x.y, y[m].y);
-            }
+        for (uint32_t g = 0; g < MK; g += 4) {
+            if (g >= nb) break;
+            ulonglong2 y[4];
+#pragma unroll
+            for (uint32_t m = 0; m < 4; m++)
+                if (g + m < nb) y[m] = __ldg(reinterpret_cast<const ulonglong2 *>(bp[g + m]) + 32 * k + lane);
+#pragma unroll
+            for (uint32_t m = 0; m < 4; m++)
+                if (g + m < nb) {
+                    x.x = apply_op(op, x.x, y[m].x);
+                    x.y = apply_op(op, x.y, y[m].y);
+                }
+        }
         D[32 * k + lane] = x;
         cc += __popcll(x.x) + __popcll(x.y);
         const uint32_t top = (uint32_t)(x.y >> 63);
