@@ -1862,14 +1862,20 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     for (uint64_t i = 0; i < nq; i++) hq[i] = {hv[p->pairs[i].a], hv[p->pairs[i].b]};
     memcpy(hbuf.data() + o_tb, tb.data(), 8ull * (nq + 1));
     {
-        std::vector<uint32_t> ord;
-        ord.reserve(nq);
+        // k_compact's order: the materialising queries by output slots,
+        // largest first, ties in query order (a counting sort: the slot
+        // counts are at most twice the largest key count)
+        uint32_t top = 0;
         for (uint64_t i = 0; i < nq; i++)
-            if (!(p->pairs[i].flags & F_COUNT) && p->pairs[i].n_pos) ord.push_back((uint32_t)i);
-        std::stable_sort(ord.begin(), ord.end(),
-                         [&](uint32_t x, uint32_t y) { return p->pairs[x].n_pos > p->pairs[y].n_pos; });
-        p->n_order = (uint32_t)ord.size();
-        if (!ord.empty()) memcpy(hbuf.data() + o_ord, ord.data(), 4ull * ord.size());
+            if (!(p->pairs[i].flags & F_COUNT)) top = std::max(top, p->pairs[i].n_pos);
+        std::vector<uint32_t> start((size_t)top + 2, 0);
+        for (uint64_t i = 0; i < nq; i++)
+            if (!(p->pairs[i].flags & F_COUNT) && p->pairs[i].n_pos) start[top - p->pairs[i].n_pos + 1]++;
+        for (size_t v = 1; v < start.size(); v++) start[v] += start[v - 1];
+        uint32_t *ord = reinterpret_cast<uint32_t *>(hbuf.data() + o_ord);
+        for (uint64_t i = 0; i < nq; i++)
+            if (!(p->pairs[i].flags & F_COUNT) && p->pairs[i].n_pos) ord[start[top - p->pairs[i].n_pos]++] = (uint32_t)i;
+        p->n_order = start[top];
     }
     cudaError_t e = cudaMallocHost((void **)&p->h_stats, sizeof(PairStats) * std::max<uint64_t>(nq, 1));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&p->h_es, sizeof(ExecState));
