@@ -358,13 +358,15 @@ __device__ __forceinline__ uint32_t keep_table(uint32_t op) {
 // input(s) it came from; counts cardinality c and runs r, and with EMIT
 // writes the kept values to out (4-byte aligned; whole words are written,
 // the upper half of an odd last word zeroed).  a and b are generic pointers:
-// the arrays staged in shared memory, or in global memory.
-template <bool EMIT>
-__device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *a, uint32_t na, const uint16_t *b,
-                                                  uint32_t nb, uint32_t &c, uint32_t &r, uint16_t *out) {
+// the arrays staged in shared memory, or in global memory.  TBL is the op's
+// table (keep_table), fixed at compile time so that each op's loop carries
+// only its own keep test.
+template <bool EMIT, uint32_t TBL>
+__device__ __forceinline__ void lane_merge_arrays_t(const uint16_t *a, uint32_t na, const uint16_t *b, uint32_t nb,
+                                                    uint32_t &c, uint32_t &r, uint16_t *out) {
     // what the table keeps: a value only a holds (bit 2), only b holds
     // (bit 0), both hold (bit 3, taken from a)
-    const bool k_a = (tbl & 4u) != 0, k_b = (tbl & 1u) != 0, k_ab = (tbl & 8u) != 0;
+    constexpr bool k_a = (TBL & 4u) != 0, k_b = (TBL & 1u) != 0, k_ab = (TBL & 8u) != 0;
     uint32_t i = 0, j = 0, last = 0xFFFFFFFEu;
     c = 0;
     r = 0;
@@ -388,6 +390,32 @@ __device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *
         j += !lt;
     }
     if (EMIT && (c & 1u)) reinterpret_cast<uint32_t *>(out)[c >> 1] = last;   // zero upper half
+}
+
+// the merge above for a table known only at run time
+template <bool EMIT>
+__device__ __forceinline__ void lane_merge_arrays(uint32_t tbl, const uint16_t *a, uint32_t na, const uint16_t *b,
+                                                  uint32_t nb, uint32_t &c, uint32_t &r, uint16_t *out) {
+    switch (tbl) {
+        case 0x8u: lane_merge_arrays_t<EMIT, 0x8u>(a, na, b, nb, c, r, out); break;
+        case 0xDu: lane_merge_arrays_t<EMIT, 0xDu>(a, na, b, nb, c, r, out); break;
+        case 0x4u: lane_merge_arrays_t<EMIT, 0x4u>(a, na, b, nb, c, r, out); break;
+        default: lane_merge_arrays_t<EMIT, 0x5u>(a, na, b, nb, c, r, out); break;
+    }
+}
+
+// |a n b| of two small sorted arrays by one lane: equal heads count and both
+// advance, otherwise the smaller head advances
+__device__ __forceinline__ uint32_t lane_count_and(const uint16_t *a, uint32_t na, const uint16_t *b, uint32_t nb) {
+    uint32_t i = 0, j = 0, c = 0;
+#pragma unroll 1
+    while (i < na && j < nb) {
+        const uint32_t va = a[i], vb = b[j];
+        c += va == vb;
+        i += va <= vb;
+        j += vb <= va;
+    }
+    return c;
 }
 
 // ------------------------------------------------------------ lean kernel
@@ -1281,7 +1309,10 @@ __device__ void process_items(const PairParams &P, const Item *q, uint32_t n, ui
     uint32_t card = 0;
     if (mode == M_LANE_ARR) {
         uint32_t c, r;
-        if (count || off == ALLOC_FAIL) {
+        if (count) {
+            c = lane_count_and(la, ca.card, lb, cb.card);
+            r = 0;
+        } else if (off == ALLOC_FAIL) {
             lane_merge_arrays<false>(tbl, la, ca.card, lb, cb.card, c, r, nullptr);
         } else {
             lane_merge_arrays<true>(tbl, la, ca.card, lb, cb.card, c, r, reinterpret_cast<uint16_t *>(es->arena + off));
