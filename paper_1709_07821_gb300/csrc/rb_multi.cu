@@ -1236,21 +1236,34 @@ rb_status multi_prepare(const rb *const *pool, const BmView *d_pool, uint32_t po
     return RB_OK;
 }
 
-// k_multi is persistent: as many CTAs per SM as fit (found once from the
-// occupancy calculator; 16 warps per SM), capped by the batch's tiles
+// CTAs of k_multi<W> resident per SM on the current device: found once per
+// device from the occupancy calculator (after raising the kernel's dynamic
+// shared-memory limit on that device); concurrent first calls store the same
+// value
+template <int W>
+static int multi_ctas_per_sm() {
+    constexpr int MAX_DEV = 256;
+    static std::atomic<int> cache[MAX_DEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    int c = dev < MAX_DEV ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (c > 0) return c;
+    const int smem = W * WARP_SMEM;
+    cudaFuncSetAttribute(k_multi<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_multi<W>, W * 32, smem) != cudaSuccess || c < 1) {
+        cudaGetLastError();
+        c = 1;
+    }
+    if (dev < MAX_DEV) cache[dev].store(c, std::memory_order_relaxed);
+    return c;
+}
+
+// k_multi is persistent: as many CTAs per SM as fit (16 warps per SM),
+// capped by the batch's tiles
 template <int W>
 static void launch_multi_w(const MParams &P, cudaStream_t s) {
-    static std::atomic<int> per_sm{0};
     const int smem = W * WARP_SMEM;
-    int ctas = per_sm.load();
-    if (ctas == 0) {
-        cudaFuncSetAttribute(k_multi<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, k_multi<W>, W * 32, smem) != cudaSuccess || ctas < 1) {
-            cudaGetLastError();
-            ctas = 1;
-        }
-        per_sm.store(ctas);
-    }
+    const int ctas = multi_ctas_per_sm<W>();
     unsigned long long need = (P.n_tiles + W - 1) / W, cap = (unsigned long long)sm_count() * ctas;
     unsigned grid = (unsigned)std::max<unsigned long long>(1, std::min(need, cap));
     // chunks of consecutive tiles only when every warp has many tiles: a

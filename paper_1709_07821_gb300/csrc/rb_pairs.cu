@@ -1691,13 +1691,18 @@ __global__ void __launch_bounds__(512) k_compact(const PairDev *pairs, const uin
 
 // ------------------------------------------------------------ host side
 
+// k_heavy's dynamic shared-memory limits, raised once per device (function
+// attributes belong to the current device's context)
 void init_kernel_attrs() {
-    static bool done = false;
-    if (done) return;
+    constexpr int MAX_DEV = 256;
+    static std::atomic<int> done[MAX_DEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return;
+    if (dev < MAX_DEV && done[dev].load(std::memory_order_relaxed)) return;
     cudaFuncSetAttribute(k_heavy<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 16384);
     cudaFuncSetAttribute(k_heavy<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 16384);
     cudaFuncSetAttribute(k_heavy<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * 16384);
-    done = true;
+    if (dev < MAX_DEV) done[dev].store(1, std::memory_order_relaxed);
 }
 
 template <int W>
