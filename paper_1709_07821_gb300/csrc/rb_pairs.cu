@@ -1713,6 +1713,8 @@ void launch_heavy_w(const PairParams &P, int ctas_per_sm, cudaStream_t s) {
 
 }  // namespace
 
+#include <thread>
+
 struct rb_plan {
     std::vector<const rb *> pool;
     std::vector<rb_query> q;
@@ -1788,6 +1790,30 @@ void query_bounds(const rb *A, const rb *B, uint32_t op, uint64_t &w, uint64_t &
 
 uint64_t lean_warps(const rb_plan *p, const rb_schedule &sc);
 
+// Host passes over a batch's queries run in up to 8 pieces of at least
+// 8,192 queries on their own threads (the caller takes the first piece):
+// building a 65,536-query plan is otherwise a few milliseconds of one core.
+uint32_t plan_pieces(uint64_t n) {
+    const uint64_t hw = std::max(1u, std::thread::hardware_concurrency());
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(std::min<uint64_t>(hw, 8), n / 8192));
+}
+template <class F>
+void parallel_pieces(uint64_t n, uint32_t pieces, F f) {
+    const uint64_t per = (n + pieces - 1) / std::max<uint32_t>(pieces, 1);
+    std::vector<std::thread> th;
+    for (uint32_t k = 1; k < pieces; k++) {
+        const uint64_t lo = k * per, hi = std::min(n, lo + per);
+        if (lo >= hi) continue;
+        try {
+            th.emplace_back(f, k, lo, hi);
+        } catch (...) {   // no thread to be had: the caller runs the piece
+            f(k, lo, hi);
+        }
+    }
+    f(0u, (uint64_t)0, std::min(n, per));
+    for (std::thread &t : th) t.join();
+}
+
 rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q, uint64_t nq, cudaStream_t s,
                      bool use_bounds, rb_plan **out) {
     *out = nullptr;
@@ -1801,8 +1827,6 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     p->q.assign(q, q + nq);
     p->pairs.resize(nq);
     std::vector<unsigned long long> tb(nq + 1);
-    uint64_t npos = 0, tiles = 0, ew = 0, eb = 0, bw = 0, bb = 0, ed = 0, small_bound = 0;
-    p->meta_bytes = 0;
     for (uint64_t i = 0; i < nq; i++) {
         const rb_query &x = q[i];
         if (x.op > 3 || x.a >= pool_n || x.b >= pool_n) {
@@ -1810,55 +1834,84 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
             return set_err(RB_EINVAL, "batch: query %llu has op %u, a %u, b %u (pool of %u)",
                            (unsigned long long)i, x.op, x.a, x.b, pool_n);
         }
-        const rb *A = pool[x.a], *B = pool[x.b];
-        PairDev &d = p->pairs[i];
-        d.a = x.a;
-        d.b = x.b;
-        d.op = x.op;
-        const bool count = (x.flags & RB_Q_COUNT_ONLY) != 0;
-        const uint64_t na = A->n, nb = B->n, mn = std::min(na, nb), mx = std::max(na, nb);
-        // merge mode unless one key list is more than 8 times the other
-        // (then a binary search per key of the smaller side is cheaper)
-        bool merge;
-        if (!count && (x.op == OP_OR || x.op == OP_XOR)) merge = true;
-        else if (!count && x.op == OP_ANDNOT) merge = !(nb * 8 < na || na * 8 < nb);
-        else merge = mx <= 8 * mn;
-        d.flags = (count ? F_COUNT : 0) | (merge ? F_MERGE : 0);
-        // the key arrays and metadata of both inputs, and a count-only result
-        p->meta_bytes += META_BYTES * (na + nb) + (count ? COUNT_BYTES : 0);
-        uint64_t ns, np;
-        if (merge) ns = na + nb;
-        else if (count || x.op == OP_AND) ns = mn;
-        else ns = na;
-        if (count) np = 0;
-        else if (x.op == OP_OR || x.op == OP_XOR) np = na + nb;
-        else if (x.op == OP_ANDNOT) np = na;
-        else np = merge ? na : mn;
-        d.n_slots = (uint32_t)ns;
-        d.n_pos = (uint32_t)np;
-        small_bound += mn;   // matched keys: at most the smaller key count
-        d.pos_base = npos;
-        npos += np;
-        ed += 2ull * (A->n_bitsets + B->n_bitsets) + ns / 16;
-        if (!count) {
-            p->any_mat = true;
-            uint64_t w1, b1;
-            query_bounds(A, B, x.op, w1, b1);
-            bw += w1;
-            bb += b1;
-            if (x.op == OP_AND) {
-                ew += std::min(A->word_bytes, B->word_bytes);
-                eb += 8192ull * std::min(A->n_bitsets, B->n_bitsets);
-            } else if (x.op == OP_ANDNOT) {
-                ew += A->word_bytes;
-                eb += 8192ull * A->n_bitsets;
-            } else {
-                ew += A->word_bytes + B->word_bytes;
-                eb += 8192ull * ((uint64_t)A->n_bitsets + B->n_bitsets);
+    }
+    // per query: its mode, slots and positions, and its share of the size
+    // estimates (in parallel pieces; the offsets are summed up after)
+    struct Sums {
+        uint64_t meta = 0, small_bound = 0, ed = 0, ew = 0, eb = 0, bw = 0, bb = 0;
+        bool any_mat = false;
+    };
+    const uint32_t pieces = plan_pieces(nq);
+    std::vector<Sums> part(pieces);
+    parallel_pieces(nq, pieces, [&](uint32_t k, uint64_t lo, uint64_t hi) {
+        Sums &S = part[k];
+        for (uint64_t i = lo; i < hi; i++) {
+            const rb_query &x = q[i];
+            const rb *A = pool[x.a], *B = pool[x.b];
+            PairDev &d = p->pairs[i];
+            d.a = x.a;
+            d.b = x.b;
+            d.op = x.op;
+            const bool count = (x.flags & RB_Q_COUNT_ONLY) != 0;
+            const uint64_t na = A->n, nb = B->n, mn = std::min(na, nb), mx = std::max(na, nb);
+            // merge mode unless one key list is more than 8 times the other
+            // (then a binary search per key of the smaller side is cheaper)
+            bool merge;
+            if (!count && (x.op == OP_OR || x.op == OP_XOR)) merge = true;
+            else if (!count && x.op == OP_ANDNOT) merge = !(nb * 8 < na || na * 8 < nb);
+            else merge = mx <= 8 * mn;
+            d.flags = (count ? F_COUNT : 0) | (merge ? F_MERGE : 0);
+            // the key arrays and metadata of both inputs, and a count-only result
+            S.meta += META_BYTES * (na + nb) + (count ? COUNT_BYTES : 0);
+            uint64_t ns, np;
+            if (merge) ns = na + nb;
+            else if (count || x.op == OP_AND) ns = mn;
+            else ns = na;
+            if (count) np = 0;
+            else if (x.op == OP_OR || x.op == OP_XOR) np = na + nb;
+            else if (x.op == OP_ANDNOT) np = na;
+            else np = merge ? na : mn;
+            d.n_slots = (uint32_t)ns;
+            d.n_pos = (uint32_t)np;
+            S.small_bound += mn;   // matched keys: at most the smaller key count
+            S.ed += 2ull * (A->n_bitsets + B->n_bitsets) + ns / 16;
+            if (!count) {
+                S.any_mat = true;
+                uint64_t w1, b1;
+                query_bounds(A, B, x.op, w1, b1);
+                S.bw += w1;
+                S.bb += b1;
+                if (x.op == OP_AND) {
+                    S.ew += std::min(A->word_bytes, B->word_bytes);
+                    S.eb += 8192ull * std::min(A->n_bitsets, B->n_bitsets);
+                } else if (x.op == OP_ANDNOT) {
+                    S.ew += A->word_bytes;
+                    S.eb += 8192ull * A->n_bitsets;
+                } else {
+                    S.ew += A->word_bytes + B->word_bytes;
+                    S.eb += 8192ull * ((uint64_t)A->n_bitsets + B->n_bitsets);
+                }
             }
         }
+    });
+    uint64_t npos = 0, tiles = 0, ew = 0, eb = 0, bw = 0, bb = 0, ed = 0, small_bound = 0;
+    p->meta_bytes = 0;
+    for (const Sums &S : part) {
+        p->meta_bytes += S.meta;
+        small_bound += S.small_bound;
+        ed += S.ed;
+        ew += S.ew;
+        eb += S.eb;
+        bw += S.bw;
+        bb += S.bb;
+        p->any_mat = p->any_mat || S.any_mat;
+    }
+    for (uint64_t i = 0; i < nq; i++) {
+        PairDev &d = p->pairs[i];
+        d.pos_base = npos;
+        npos += d.n_pos;
         tb[i] = tiles;
-        tiles += (ns + 31) / 32;
+        tiles += (d.n_slots + 31) / 32;
     }
     tb[nq] = tiles;
     p->total_pos = npos;
@@ -1895,7 +1948,9 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
     for (uint32_t i = 0; i < pool_n; i++) hv[i] = view_of(pool[i]);
     if (nq) memcpy(hbuf.data() + o_pairs, p->pairs.data(), sizeof(PairDev) * nq);
     QViews *hq = (QViews *)(hbuf.data() + o_qv);
-    for (uint64_t i = 0; i < nq; i++) hq[i] = {hv[p->pairs[i].a], hv[p->pairs[i].b]};
+    parallel_pieces(nq, pieces, [&](uint32_t, uint64_t lo, uint64_t hi) {
+        for (uint64_t i = lo; i < hi; i++) hq[i] = {hv[p->pairs[i].a], hv[p->pairs[i].b]};
+    });
     memcpy(hbuf.data() + o_tb, tb.data(), 8ull * (nq + 1));
     {
         // k_compact's order: the materialising queries by output slots,
