@@ -188,7 +188,7 @@ typedef struct {
  * materialising query and NULL for a count-only one (outs may be NULL when
  * every query is count-only); counts[i] (counts may be NULL) receives the
  * result's cardinality.  Results are identical to nq separate rb_apply /
- * rb_apply_cardinality calls.  Preparing a batch of more than 16,384
+ * rb_apply_cardinality calls.  Preparing a batch of 16,384 or more
  * queries (here and in rb_plan_create) spreads its per-query host passes
  * over up to 8 short-lived threads, joined before the call returns. */
 rb_status rb_batch_op(const rb_t *const *pool, uint32_t pool_n, const rb_query *q, uint64_t nq,
