@@ -252,8 +252,8 @@ void rb_plan_free(rb_plan_t *p);
  * ahead of use (0 = none); and how many consecutive 32-slot tiles a lean
  * kernel warp takes from the shared work counter at once (1 .. 256; 0 =
  * 32; plans too small to give every warp about 64 takes of that size take
- * fewer).  The multi-way kernel (rb_multi_op, accumulators, the serving
- * loop) takes warps_per_cta from here and runs as many CTAs per SM as fit. */
+ * fewer).  The multi-way kernel (rb_multi_op and the serving loop) takes
+ * warps_per_cta from here and runs as many CTAs per SM as fit. */
 typedef struct {
     uint32_t warps_per_cta;
     uint32_t ctas_per_sm;
