@@ -1794,7 +1794,8 @@ uint64_t lean_warps(const rb_plan *p, const rb_schedule &sc);
 // 8,192 queries on their own threads (the caller takes the first piece):
 // building a 65,536-query plan is otherwise a few milliseconds of one core.
 uint32_t plan_pieces(uint64_t n) {
-    const uint64_t hw = std::max(1u, std::thread::hardware_concurrency());
+    if (n < 2 * 8192) return 1;
+    static const uint64_t hw = std::max(1u, std::thread::hardware_concurrency());   // read once
     return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(std::min<uint64_t>(hw, 8), n / 8192));
 }
 template <class F>
@@ -1952,10 +1953,21 @@ rb_status plan_build(const rb_t *const *pool, uint32_t pool_n, const rb_query *q
         for (uint64_t i = lo; i < hi; i++) hq[i] = {hv[p->pairs[i].a], hv[p->pairs[i].b]};
     });
     memcpy(hbuf.data() + o_tb, tb.data(), 8ull * (nq + 1));
-    {
+    if (nq < 4096) {
         // k_compact's order: the materialising queries by output slots,
-        // largest first, ties in query order (a counting sort: the slot
-        // counts are at most twice the largest key count)
+        // largest first, ties in query order
+        std::vector<uint32_t> ord;
+        ord.reserve(nq);
+        for (uint64_t i = 0; i < nq; i++)
+            if (!(p->pairs[i].flags & F_COUNT) && p->pairs[i].n_pos) ord.push_back((uint32_t)i);
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](uint32_t x, uint32_t y) { return p->pairs[x].n_pos > p->pairs[y].n_pos; });
+        p->n_order = (uint32_t)ord.size();
+        if (!ord.empty()) memcpy(hbuf.data() + o_ord, ord.data(), 4ull * ord.size());
+    } else {
+        // the same order for large batches by a counting sort (the slot
+        // counts are at most twice the largest key count; a comparison sort
+        // of 65,536 queries took 3.6 ms)
         uint32_t top = 0;
         for (uint64_t i = 0; i < nq; i++)
             if (!(p->pairs[i].flags & F_COUNT)) top = std::max(top, p->pairs[i].n_pos);
