@@ -103,11 +103,11 @@ __device__ uint64_t alloc_b(MState *es, uint32_t lane) {
 // output key).  A key whose containers are all arrays with at most LCAP
 // values in play is then merged by its own lane (OR: one k-way merge of the
 // sorted arrays; AND: the smallest array filtered by binary search in the
-// others) from its arrays staged in its share of the warp's tiles,
-// straight into its output; the other keys are folded by the whole warp in
-// the tiles, as the general path does.
+// others) from its arrays staged in its share of the warp's 8 KB shared
+// tile, straight into its output; the other keys are folded by the whole
+// warp in that shared tile, as the general path does.
 constexpr uint32_t MK = 8;
-constexpr uint32_t LCAP = 1024;  // values in play that one lane merges alone (the rest: the warp, in tiles)
+constexpr uint32_t LCAP = 1024;  // values in play that one lane merges alone (the rest: the warp's folds)
 constexpr uint32_t STAGE_WORDS = 2048;   // the warp's tile, shared out to its lanes by a prefix sum
 constexpr uint32_t NOIX = 0xFFFFFFFFu;
 constexpr uint32_t MKEY_END = 0x10000u;
